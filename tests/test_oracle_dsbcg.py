@@ -1,0 +1,156 @@
+"""Pins for the oracle's DSBlockCG (CPU only).
+
+The oracle's recurrences are checked against
+  * dense LU solves of every (sigma_j I + A) x = b (Eq. 1.1) on 2^4 and 4^4,
+  * the Galerkin definition X = V (V^H (sigma+A) V)^{-1} V^H B over the block
+    Krylov subspace (Eqs. 2.1, 2.2, 3.2), with a basis built by fully
+    orthogonalised block Arnoldi, at a fixed number of block steps,
+  * textbook CG iterates for m = s = 1,
+  * exact deflation when b_4 = b_1 + b_2 (Sec. 3: the deflated subspace has
+    smaller dimension and the bandwidth of T drops),
+  * the structural statements of Sec. 3: orthonormal V, hermitian banded T
+    with semi-bandwidth m, T = V^H A V, B = V rho.
+"""
+import numpy as np
+import pytest
+
+from oracle import wilson as W
+from oracle.dsbcg import NotHPD, dense_solve, dsbcg, galerkin_iterate, true_relres
+from paper_1205_0359_gb300 import synth
+
+
+def _problem(dims, m, s, seed, eps=0.4, kappa=0.12, dependent=False):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    U = synth.su3_links(dims, eps, rng)
+    n = 12 * synth.volume(dims)
+    B = synth.gaussian_rhs(n, m, rng)
+    if dependent:
+        B[m - 1] = B[0] + B[1]
+    sigma = synth.log_shifts(1e-3, 1.0, s)
+    Aop = lambda v: W.A_vec(U, kappa, dims, v)
+    return U, kappa, B, sigma, Aop
+
+
+@pytest.fixture(scope="module")
+def small():
+    dims = (2, 2, 2, 2)
+    U, kappa, B, sigma, Aop = _problem(dims, 3, 4, 21)
+    Ad = W.dense_A(U, kappa, dims)
+    return dims, Ad, B, sigma, Aop
+
+
+@pytest.fixture(scope="module")
+def w1():
+    wl = synth.make_workload("w1_4x4x4x4")
+    dims, U, k = wl["dims"], wl["U"], wl["kappa"]
+    Ad = W.dense_A(U, k, dims)
+    Aop = lambda v: W.A_vec(U, k, dims, v)
+    return wl, Ad, Aop
+
+
+def test_dense_lu_2x2x2x2(small):
+    dims, Ad, B, sigma, Aop = small
+    X, info = dsbcg(Aop, B, sigma, tol=1e-13)
+    Xd = dense_solve(Ad, B, sigma)
+    err = np.linalg.norm(X - Xd, axis=2) / np.linalg.norm(Xd, axis=2)
+    assert info["converged"]
+    assert err.max() < 1e-10
+
+
+def test_dense_lu_4x4x4x4_workload(w1):
+    wl, Ad, Aop = w1
+    B, sigma = wl["B"], wl["sigma"]
+    X, info = dsbcg(Aop, B, sigma, tol=1e-12)
+    Xd = dense_solve(Ad, B, sigma)
+    err = np.linalg.norm(X - Xd, axis=2) / np.linalg.norm(Xd, axis=2)
+    assert info["converged"]
+    assert info["deflations"] >= 1
+    assert err.max() < 1e-9
+    rr = true_relres(Aop, B, sigma, X)
+    assert rr.max() <= 1e-12
+
+
+@pytest.mark.parametrize("nblocks", [1, 2, 3])
+def test_galerkin_definition_fixed_k(small, nblocks):
+    dims, Ad, B, sigma, Aop = small
+    m = B.shape[0]
+    X, info = dsbcg(Aop, B, sigma, tol=0.0, freeze=False, stop_after_vectors=m * nblocks)
+    assert info["nvec"] == m * nblocks
+    Xg = galerkin_iterate(Ad, B, sigma, nblocks)
+    err = np.linalg.norm(X - Xg, axis=2) / np.linalg.norm(Xg, axis=2)
+    assert err.max() < 1e-9
+
+
+def test_galerkin_definition_with_deflation(w1):
+    wl, Ad, Aop = w1
+    B, sigma = wl["B"], wl["sigma"]
+    # b_4 = b_1 + b_2: the block Krylov space has dimension 3 per block
+    for nblocks in (1, 2):
+        X, info = dsbcg(Aop, B, sigma, tol=0.0, freeze=False, stop_after_vectors=3 * nblocks)
+        if nblocks > 1:          # b_4 is examined once v_1..v_3 exist
+            assert info["deflations"] == 1 and info["deflated_at"] == [3]
+        Xg = galerkin_iterate(Ad, B, sigma, nblocks)
+        err = np.linalg.norm(X - Xg, axis=2) / np.linalg.norm(Xg, axis=2)
+        assert err.max() < 1e-9
+
+
+def test_textbook_cg_m1_s1(small):
+    """m = s = 1: the iterates are those of plain CG on (sigma + A) x = b."""
+    dims, Ad, B, sigma, Aop = small
+    b = B[0]
+    sg = sigma[1]
+    M = Ad + sg * np.eye(Ad.shape[0])
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    for k in range(1, 9):
+        Mp = M @ p
+        a = np.vdot(r, r).real / np.vdot(p, Mp).real
+        x = x + a * p
+        rn = r - a * Mp
+        beta = np.vdot(rn, rn).real / np.vdot(r, r).real
+        p = rn + beta * p
+        r = rn
+        Xo, _ = dsbcg(Aop, b[None], [sg], tol=0.0, freeze=False, stop_after_vectors=k)
+        assert np.linalg.norm(Xo[0, 0] - x) <= 1e-10 * np.linalg.norm(x)
+
+
+def test_exact_deflation_solution(w1):
+    wl, Ad, Aop = w1
+    B, sigma = wl["B"], wl["sigma"]
+    X, info = dsbcg(Aop, B, sigma, tol=1e-13, freeze=False)
+    assert info["deflated_at"][0] == 3
+    diff = np.linalg.norm(X[:, 3] - X[:, 0] - X[:, 1], axis=1) / np.linalg.norm(X[:, 3], axis=1)
+    assert diff.max() < 1e-11
+
+
+def test_lanczos_structure(small):
+    dims, Ad, B, sigma, Aop = small
+    m = B.shape[0]
+    X, info = dsbcg(Aop, B, sigma, tol=0.0, freeze=False, stop_after_vectors=5 * m,
+                    keep_basis=True)
+    V, T, rho = info["V"], info["T"], info["rho"]
+    k = V.shape[0]
+    assert np.max(np.abs(V.conj() @ V.T - np.eye(k))) < 1e-10
+    assert np.max(np.abs(T - T.conj().T)) == 0.0
+    i, j = np.nonzero(np.abs(T) > 0)
+    assert np.max(np.abs(i - j)) <= m                 # semi-bandwidth m (Sec. 3)
+    TA = V.conj() @ Ad @ V.T                           # V^H A V
+    assert np.max(np.abs(T - TA)) < 1e-10
+    assert np.max(np.abs(V.T @ rho - B.T)) < 1e-12    # B = V rho
+    assert np.max(np.abs(np.tril(rho, -1)[m:])) == 0.0
+
+
+def test_shifted_systems_share_one_lanczos_run(small):
+    """One multi-shift run equals separate single-shift runs (Sec. 3, last paragraph)."""
+    dims, Ad, B, sigma, Aop = small
+    X, _ = dsbcg(Aop, B, sigma, tol=0.0, freeze=False, stop_after_vectors=12)
+    for j, sg in enumerate(sigma):
+        Xj, _ = dsbcg(Aop, B, [sg], tol=0.0, freeze=False, stop_after_vectors=12)
+        assert np.max(np.abs(X[j] - Xj[0])) < 1e-12 * np.max(np.abs(Xj))
+
+
+def test_not_hpd_is_reported(small):
+    dims, Ad, B, sigma, Aop = small
+    with pytest.raises(NotHPD):
+        dsbcg(Aop, B, [-10.0], tol=1e-10)
