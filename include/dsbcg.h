@@ -1,0 +1,176 @@
+/*
+ * dsbcg.h -- C ABI of the GB300 (sm_103a) implementation of the deflated
+ * shifted block CG method (DSBlockCG) of Birk & Frommer, "A CG Method for
+ * Multiple Right Hand Sides and Multiple Shifts in Lattice QCD Calculations"
+ * (Lattice 2011, arXiv:1205.0359).
+ *
+ * Problem (Sec. 1, Eqs. 1.1 and 1.2):
+ *     (sigma_j I + A) X_j = B,   j = 1..s,   B = [b_1 | ... | b_m],
+ * with A = D^H D, D the Wilson-Dirac operator on a 4D lattice, and
+ * sigma_j >= 0 real so that sigma_j I + A is hermitian positive definite.
+ *
+ * Conventions shared by every entry point:
+ *   site index   site = x + Lx*(y + Ly*(z + Lz*t))
+ *   vector index site*12 + spin*3 + colour, complex128 (n = 12 * volume)
+ *   gauge field  complex128 [site][mu = x,y,z,t][row][col]
+ *   D psi(x) = psi(x) - kappa * sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu)
+ *                                      + (1 + gamma_mu) U_mu(x-mu)^H psi(x-mu) ],
+ *   chiral gamma basis (gamma_5 = diag(-1,-1,1,1)), periodic in space, and
+ *   antiperiodic in time when t_antiperiodic != 0.  D^H = gamma_5 D gamma_5.
+ *
+ * Pointers: "device or host" arguments may point to device memory or to host
+ * memory (pageable or pinned); the library detects which and copies host
+ * data in and out on the context's stream.  The caller owns every buffer it
+ * passes; the library never frees them.  A context owns its workspace and its
+ * packed copies of the gauge field.
+ *
+ * Errors: every call returns a dsbcg_status; nothing is thrown across the
+ * ABI.  After DSBCG_ERR_CUDA the context should be destroyed.
+ * Thread safety: one context must not be used by two host threads at once.
+ */
+#ifndef DSBCG_H
+#define DSBCG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dsbcg_ctx dsbcg_ctx;
+
+typedef enum {
+    DSBCG_OK = 0,
+    DSBCG_NOT_CONVERGED = 1,   /* iteration or restart cap reached; X holds the best iterate */
+    DSBCG_ERR_ARG = -1,        /* invalid argument (size, null pointer, negative shift, ...) */
+    DSBCG_ERR_NOT_HPD = -2,    /* a pivot d_k of sigma_j I + T was <= 0 */
+    DSBCG_ERR_CUDA = -3,       /* a CUDA runtime call failed */
+    DSBCG_ERR_OOM = -4,        /* device allocation failed */
+    DSBCG_ERR_NONFINITE = -5,  /* NaN or Inf in an input */
+    DSBCG_ERR_UNSUPPORTED = -6 /* option not supported by this build */
+} dsbcg_status;
+
+/* Storage precision of spinor fields and links inside the Krylov iteration.
+ * Arithmetic on FP32/BF16/FP16 storage is FP32; the m x m block coefficients,
+ * deflation, per-shift recurrences and true residuals are always FP64. */
+typedef enum {
+    DSBCG_PREC_FP64 = 0,
+    DSBCG_PREC_FP32 = 1,
+    DSBCG_PREC_BF16 = 2,
+    DSBCG_PREC_FP16 = 3
+} dsbcg_prec;
+
+/* Operators for dsbcg_apply. */
+typedef enum {
+    DSBCG_OP_D = 0,      /* D */
+    DSBCG_OP_DDAG = 1,   /* D^H = gamma_5 D gamma_5 */
+    DSBCG_OP_A = 2       /* A = D^H D */
+} dsbcg_op;
+
+typedef struct {
+    int storage;            /* dsbcg_prec of the inner Krylov iteration (default FP32) */
+    double dtol;            /* deflation threshold relative to a direction's norm when
+                               created; <= 0 selects the default for the precision */
+    int max_block_steps;    /* cap on block Lanczos steps over the whole solve */
+    int max_restarts;       /* cap on FP64 true-residual restarts */
+    double restart_drop;    /* an inner solve stops once every estimated residual has
+                               dropped by this factor (mixed precision only) */
+    int poll_every;         /* block steps between host reads of the convergence flags */
+    int freeze_converged;   /* stop updating converged (i, j) systems (Sec. 4) */
+    int refine;             /* 1: after the joint solve, restart each unconverged shift
+                               separately (block CG) until its true residual meets tol */
+} dsbcg_params;
+
+typedef struct {
+    int block_steps;        /* block Lanczos steps, all inner solves */
+    long long mvms;         /* A applications to single vectors (one D plus one D^H each) */
+    int deflations;         /* directions dropped by deflation */
+    int restarts;           /* FP64 true-residual restarts */
+    int final_rank;         /* block width m_k at the end of the last inner solve */
+    double seconds;         /* wall time of the call */
+    double* true_relres;    /* caller-provided [s][m] or NULL: final FP64 true
+                               residual ||b_i - (sigma_j + A) x_ij|| / ||b_i|| */
+    int* conv_step;         /* caller-provided [s][m] or NULL: block step at which
+                               (i, j) met its inner target (-1: never) */
+    double kernel_ms[8];    /* if profiling is on: summed CUDA-event time per kernel
+                               class (see DSBCG_KCLASS_*) */
+    long long kernel_launches[8];
+} dsbcg_stats;
+
+/* kernel classes reported in dsbcg_stats.kernel_ms */
+#define DSBCG_KCLASS_DSLASH 0       /* Wilson hopping stencil */
+#define DSBCG_KCLASS_GRAM 1         /* tall-skinny Gram products */
+#define DSBCG_KCLASS_UPDATE 2       /* block update W = Y - V a - V' b^H (+ Gram) */
+#define DSBCG_KCLASS_SHIFT 3        /* fused shift update (V, P_j, X_j) */
+#define DSBCG_KCLASS_SMALL 4        /* FP64 m x m kernels */
+#define DSBCG_KCLASS_RESIDUAL 5     /* FP64 true residual */
+#define DSBCG_KCLASS_OTHER 6
+
+/* Fill *p with the defaults (FP32 storage, automatic dtol, freezing on). */
+void dsbcg_params_default(dsbcg_params* p);
+
+/* Create a context for one lattice and gauge field.
+ *   dims:  {Lx, Ly, Lz, Lt}, each >= 2 (the problem of Sec. 1 on a 4D lattice)
+ *   gauge: device or host complex128 [site][4][3][3]; copied and packed
+ *   kappa: hopping parameter of D
+ *   stream: cudaStream_t to run on (NULL = legacy default stream)
+ * Returns DSBCG_ERR_NONFINITE if the gauge field has NaN/Inf. */
+dsbcg_status dsbcg_create(dsbcg_ctx** out, const int dims[4], const void* gauge,
+                          double kappa, int t_antiperiodic, void* stream);
+
+/* Replace the gauge field of an existing context (same dims). */
+dsbcg_status dsbcg_update_gauge(dsbcg_ctx* ctx, const void* gauge);
+
+/* Solve (sigma_j I + A) X_j = B for j = 1..s with one block Lanczos process
+ * (Sec. 3).  The paper's iterate X^(k) = V (sigma I + T)^{-1} V^H B (Eq. 3.2)
+ * is advanced by short recurrences from a root-free (block) Cholesky
+ * factorisation of sigma_j I + T per shift; directions that become linearly
+ * dependent are deflated (Sec. 1, Sec. 3).  With FP32/BF16/FP16 storage the
+ * Krylov iteration runs in reduced precision inside an FP64 loop that
+ * recomputes true residuals and restarts (reliable updates).
+ *   m:     number of right-hand sides, 1 <= m <= 32
+ *   B:     device or host complex128 [m][n]
+ *   s:     number of shifts, 1 <= s <= 64
+ *   sigma: HOST double[s], each >= 0
+ *   tol:   target ||b_i - (sigma_j + A) x_ij|| <= tol ||b_i|| for every (i, j)
+ *   X:     device or host complex128 [s][m][n]; output (its input value is ignored)
+ *   params: NULL for defaults
+ *   stats: NULL or caller-owned
+ * Returns DSBCG_OK when every true FP64 relative residual meets tol,
+ * DSBCG_NOT_CONVERGED (X still written) when a cap is hit. */
+dsbcg_status dsbcg_solve(dsbcg_ctx* ctx, int m, const void* B, int s, const double* sigma,
+                         double tol, const dsbcg_params* params, void* X, dsbcg_stats* stats);
+
+/* Apply D, D^H or A to m fields: out_i = op(in_i).  The fields are converted
+ * to `storage` precision, the stencil runs in that precision (FP32
+ * arithmetic for reduced precisions), and the result is converted back.
+ *   in, out: device or host complex128 [m][n]; they may not overlap. */
+dsbcg_status dsbcg_apply(dsbcg_ctx* ctx, int op, int storage, int m, const void* in, void* out);
+
+/* Gauge-link gradient ("fermion force") of a real loss through the solves
+ * X_j = (sigma_j + A)^{-1} B, given adjoint solutions Lambda_j =
+ * (sigma_j + A)^{-1} G_j of the incoming gradients G_j = dL/dX_j:
+ *   dU_mu(y) = kappa sum_j w_j sum_i [F(D x_ij, lambda_ij) + F(D lambda_ij, x_ij)]_mu(y),
+ *   F(a, b)_mu(y) = sum_spin [(1-gamma_mu) a(y)] (x) conj(b(y+mu))
+ *                 + sum_spin [(1+gamma_mu) b(y)] (x) conj(a(y+mu)),
+ * with the time-boundary sign on the hop.  Complex gradients follow the
+ * dL/dRe + i dL/dIm convention.  Not in the paper (its motivation is the RHMC
+ * force, Sec. 1).
+ *   X, Lambda: device or host complex128 [s][m][n]
+ *   weights:   HOST double[s] (NULL = all ones)
+ *   dU:        device or host complex128 [site][4][3][3], overwritten
+ *   storage:   precision of the fields inside the kernel (FP64 or FP32) */
+dsbcg_status dsbcg_force(dsbcg_ctx* ctx, int m, int s, const void* X, const void* Lambda,
+                         const double* weights, int storage, void* dU);
+
+/* Per-kernel CUDA-event timing inside dsbcg_solve (off by default). */
+dsbcg_status dsbcg_set_profiling(dsbcg_ctx* ctx, int on);
+
+void dsbcg_destroy(dsbcg_ctx* ctx);
+const char* dsbcg_error_string(dsbcg_status status);
+
+/* Library build identification: "dsbcg <version> sm_103a". */
+const char* dsbcg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DSBCG_H */

@@ -1,0 +1,89 @@
+// Launchers of the tall-skinny block kernels (kernel bodies in blas_impl.cuh):
+// the Gram products here for every storage precision, the block update,
+// basis initialisation and fused shift update dispatched to the
+// per-precision translation units blas_<prec>.cu (compiled in parallel).
+#include "blas_impl.cuh"
+
+namespace dsbcg {
+using namespace blas_impl;
+
+size_t gram_partial_doubles(int nf_max) { return (size_t)ntiles_of(nf_max, 0) * 1024 * GSLOTS; }
+
+int gram_blocks(size_t n, int nf_max) {
+    int tiles = ntiles_of(nf_max, 0);
+    int nb = (152 * 4 + tiles - 1) / tiles;
+    size_t maxb = (n + GT - 1) / GT;
+    if ((size_t)nb > maxb) nb = (int)maxb;
+    if (nb < 1) nb = 1;
+    if (nb > 1024) nb = 1024;
+    return nb;
+}
+
+void launch_gram(int prec, const void* X, const void* Y, size_t ld, size_t n, const Ctl* ctl, int nf_static,
+                 int nf_max, int herm, int diag_yy, double* partials, int nblk, float hscale, cudaStream_t st) {
+    dim3 grid(ntiles_of(nf_max, herm), nblk);
+    switch (prec) {
+        case P64: gram_kernel<P64><<<grid, GT, 0, st>>>((const double2*)X, (const double2*)Y, ld, n, ctl, nf_static, nf_max, herm, diag_yy, partials, hscale); break;
+        case P32: gram_kernel<P32><<<grid, GT, 0, st>>>((const float2*)X, (const float2*)Y, ld, n, ctl, nf_static, nf_max, herm, diag_yy, partials, hscale); break;
+        case PBF16: gram_kernel<PBF16><<<grid, GT, 0, st>>>((const __nv_bfloat162*)X, (const __nv_bfloat162*)Y, ld, n, ctl, nf_static, nf_max, herm, diag_yy, partials, hscale); break;
+        case PF16: gram_kernel<PF16><<<grid, GT, 0, st>>>((const __half2*)X, (const __half2*)Y, ld, n, ctl, nf_static, nf_max, herm, diag_yy, partials, hscale); break;
+    }
+}
+
+void launch_gram_reduce(const double* partials, int nblk, int nf_max, int herm, int diag_yy, double2* G,
+                        double* diag, const Ctl* ctl, int nf_static, cudaStream_t st) {
+    (void)nf_static;
+    gram_reduce_kernel<<<ntiles_of(nf_max, herm), 64, 0, st>>>(partials, nblk, nf_max, herm, diag_yy, G, diag, ctl);
+}
+
+#define EXTERN_P(P)                                                                                      \
+    extern template void launch_bu_t<P>(void*, const void*, const void*, const void*, size_t, size_t, const Ctl*, \
+                                        int, const void*, const void*, float, cudaStream_t);                 \
+    extern template void launch_ib_t<P>(void*, size_t, const double2*, size_t, size_t, const double2*,        \
+                                        const Ctl*, int, float, cudaStream_t);                               \
+    extern template void launch_su_t<P>(void*, const void*, const void*, size_t, void*, void*, size_t, size_t,  \
+                                        int, int, const Ctl*, int, const void*, const void*, const void*,     \
+                                        const int*, float, cudaStream_t);
+namespace blas_impl {
+EXTERN_P(P64)
+EXTERN_P(P32)
+EXTERN_P(PBF16)
+EXTERN_P(PF16)
+}  // namespace blas_impl
+#undef EXTERN_P
+
+void launch_block_update(int prec, void* W, const void* Y, const void* Vk, const void* Vp, size_t ld, size_t n,
+                         const Ctl* ctl, int nf_max, const void* coef_a, const void* coef_bh, float hscale,
+                         cudaStream_t st) {
+    switch (prec) {
+        case P64: launch_bu_t<P64>(W, Y, Vk, Vp, ld, n, ctl, nf_max, coef_a, coef_bh, hscale, st); break;
+        case P32: launch_bu_t<P32>(W, Y, Vk, Vp, ld, n, ctl, nf_max, coef_a, coef_bh, hscale, st); break;
+        case PBF16: launch_bu_t<PBF16>(W, Y, Vk, Vp, ld, n, ctl, nf_max, coef_a, coef_bh, hscale, st); break;
+        case PF16: launch_bu_t<PF16>(W, Y, Vk, Vp, ld, n, ctl, nf_max, coef_a, coef_bh, hscale, st); break;
+    }
+}
+
+void launch_init_basis(int prec, void* V1, size_t ldv, const double2* B, size_t ldb, size_t n, const double2* S,
+                       const Ctl* ctl, int nf_in, float hscale, cudaStream_t st) {
+    switch (prec) {
+        case P64: launch_ib_t<P64>(V1, ldv, B, ldb, n, S, ctl, nf_in, hscale, st); break;
+        case P32: launch_ib_t<P32>(V1, ldv, B, ldb, n, S, ctl, nf_in, hscale, st); break;
+        case PBF16: launch_ib_t<PBF16>(V1, ldv, B, ldb, n, S, ctl, nf_in, hscale, st); break;
+        case PF16: launch_ib_t<PF16>(V1, ldv, B, ldb, n, S, ctl, nf_in, hscale, st); break;
+    }
+}
+
+void launch_shift_update(int prec, int wprec, void* Vnext, const void* W, const void* Vk, size_t ld, void* P,
+                         void* X, size_t ldw, size_t n, int s, int m, const Ctl* ctl, int nf_max,
+                         const void* coefS, const void* coefU, const void* coefL, const int* active,
+                         float hscale, cudaStream_t st) {
+    (void)wprec;
+    switch (prec) {
+        case P64: launch_su_t<P64>(Vnext, W, Vk, ld, P, X, ldw, n, s, m, ctl, nf_max, coefS, coefU, coefL, active, hscale, st); break;
+        case P32: launch_su_t<P32>(Vnext, W, Vk, ld, P, X, ldw, n, s, m, ctl, nf_max, coefS, coefU, coefL, active, hscale, st); break;
+        case PBF16: launch_su_t<PBF16>(Vnext, W, Vk, ld, P, X, ldw, n, s, m, ctl, nf_max, coefS, coefU, coefL, active, hscale, st); break;
+        case PF16: launch_su_t<PF16>(Vnext, W, Vk, ld, P, X, ldw, n, s, m, ctl, nf_max, coefS, coefU, coefL, active, hscale, st); break;
+    }
+}
+
+}  // namespace dsbcg

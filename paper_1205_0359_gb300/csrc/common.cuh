@@ -1,0 +1,162 @@
+// Shared device-side definitions: storage precisions, complex arithmetic,
+// internal field layout and the device-resident control block of a solve.
+//
+// Internal field layout (every kernel of the Krylov iteration uses it).
+// A field is one complex n-vector, n = 12 * V, stored pair-chunked:
+//     [pair c = sc / 2][site][2 complex]
+// for every storage precision, so that kernels mixing precisions (FP64
+// right-hand sides -> FP32 basis, FP32 iterates -> FP64 accumulators) see
+// the same element order.  Complex component sc = spin*3 + colour of site x
+// is element (sc/2 * V + x) * 2 + sc % 2.  A warp reading one pair of 32
+// consecutive sites touches one contiguous 512 B (FP32), 1 KB (FP64) or
+// 256 B (16-bit) span.  Kernels that treat a field as a flat vector (inner
+// products, block updates) see it as n complex values in this order; the
+// permutation does not change inner products.
+//
+// 16-bit fields hold value * hscale, with hscale a power of two close to
+// sqrt(n): Krylov vectors have unit norm, so their entries are O(1/sqrt(n))
+// and the scaled entries are O(1), well inside FP16's range.
+//
+// Links: [mu][entry e = row*3 + col][site] of the field precision's complex
+// storage type (U_mu(x) for the forward hop; the backward hop reads the link
+// of x - mu and applies its adjoint).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace dsbcg {
+
+enum Prec { P64 = 0, P32 = 1, PBF16 = 2, PF16 = 3 };
+
+constexpr int M_MAX = 32;      // largest block width (right-hand sides in a block)
+constexpr int S_MAX = 64;      // largest number of shifts
+
+// ------------------------------------------------------------------ traits --
+template <int P> struct Tr;
+template <> struct Tr<P64> {
+    using S2 = double2;            // complex storage element
+    using R = double;              // arithmetic real type
+    using C = double2;             // arithmetic complex type
+};
+template <> struct Tr<P32> {
+    using S2 = float2;
+    using R = float;
+    using C = float2;
+};
+template <> struct Tr<PBF16> {
+    using S2 = __nv_bfloat162;
+    using R = float;
+    using C = float2;
+};
+template <> struct Tr<PF16> {
+    using S2 = __half2;
+    using R = float;
+    using C = float2;
+};
+
+__host__ __device__ constexpr int prec_bytes(int p) {
+    return p == P64 ? 16 : (p == P32 ? 8 : 4);     // bytes per complex
+}
+
+// ---------------------------------------------------------------- complex --
+__device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+
+template <class C> __device__ __forceinline__ C cadd(C a, C b) { return mk(a.x + b.x, a.y + b.y); }
+template <class C> __device__ __forceinline__ C csub(C a, C b) { return mk(a.x - b.x, a.y - b.y); }
+template <class C> __device__ __forceinline__ C cmul(C a, C b) {
+    return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+template <class C> __device__ __forceinline__ C cmulc(C a, C b) {
+    return mk(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+// acc += a * b
+template <class C> __device__ __forceinline__ void cfma(C& acc, C a, C b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+template <class C> __device__ __forceinline__ void cfmac(C& acc, C a, C b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(-a.y, b.x, acc.y);
+}
+// acc -= a * b
+template <class C> __device__ __forceinline__ void cfms(C& acc, C a, C b) {
+    acc.x = fma(-a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(-a.x, b.y, acc.y);
+    acc.y = fma(-a.y, b.x, acc.y);
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+// i * a
+template <class C> __device__ __forceinline__ C ctimesi(C a) { return mk(-a.y, a.x); }
+
+// ------------------------------------------------------- element load/store --
+// Flat complex element i of a field (internal order), converted to the
+// arithmetic type; `inv` undoes the 16-bit scale on load, `sc` applies it on
+// store (both 1 for FP32/FP64).
+template <int P> struct Elem;
+template <> struct Elem<P64> {
+    static __device__ __forceinline__ double2 ld(const double2* p, size_t i, double) { return p[i]; }
+    static __device__ __forceinline__ void st(double2* p, size_t i, double2 v, double) { p[i] = v; }
+};
+template <> struct Elem<P32> {
+    static __device__ __forceinline__ float2 ld(const float2* p, size_t i, float) { return p[i]; }
+    static __device__ __forceinline__ void st(float2* p, size_t i, float2 v, float) { p[i] = v; }
+};
+template <> struct Elem<PBF16> {
+    static __device__ __forceinline__ float2 ld(const __nv_bfloat162* p, size_t i, float inv) {
+        float2 f = __bfloat1622float2(p[i]);
+        return make_float2(f.x * inv, f.y * inv);
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat162* p, size_t i, float2 v, float sc) {
+        p[i] = __float22bfloat162_rn(make_float2(v.x * sc, v.y * sc));
+    }
+};
+template <> struct Elem<PF16> {
+    static __device__ __forceinline__ float2 ld(const __half2* p, size_t i, float inv) {
+        float2 f = __half22float2(p[i]);
+        return make_float2(f.x * inv, f.y * inv);
+    }
+    static __device__ __forceinline__ void st(__half2* p, size_t i, float2 v, float sc) {
+        p[i] = __float22half2_rn(make_float2(v.x * sc, v.y * sc));
+    }
+};
+
+// index of complex component sc of site x inside a field (internal order)
+// (the same order for every precision P)
+template <int P> __host__ __device__ __forceinline__ size_t fidx(size_t V, size_t x, int sc) {
+    return ((size_t)(sc >> 1) * V + x) * 2 + (sc & 1);
+}
+
+// -------------------------------------------------------------- control --
+// Device-resident state of one inner solve.  Every kernel of a block step
+// reads it, so the host can enqueue steps without knowing the block widths
+// (which deflation changes on the device).
+struct Ctl {
+    int k;            // block step, 1-based (V_k is the current block)
+    int mk;           // width of V_k
+    int mprev;        // width of V_{k-1}
+    int mnext;        // width of V_{k+1} (set by the QR kernel)
+    int done;         // 1: every system frozen, or invariant subspace reached
+    int status;       // 0 ok, else a dsbcg_status error code
+    int nact;         // shifts still active
+    int deflations;   // directions dropped so far
+    long long mvms;   // single-vector A applications
+    int last_step;    // last step that did work
+    int pad[6];
+};
+
+// error codes mirrored from dsbcg.h
+constexpr int ST_NOT_HPD = -2;
+
+}  // namespace dsbcg

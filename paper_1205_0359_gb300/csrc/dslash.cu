@@ -1,0 +1,345 @@
+// Multi-right-hand-side Wilson-Dirac stencil (the operator of Sec. 1).
+//
+//   (D psi)(x) = psi(x) - kappa * sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu)
+//                                        + (1 + gamma_mu) U_mu(x-mu)^H psi(x-mu) ]
+//
+// One CTA covers 32 consecutive sites and every field of the block
+// (blockDim = 32 x nf_max).  The 8 links a site needs (4 forward, 4 backward)
+// are staged once per CTA in shared memory and applied to all fields, so each
+// link is read from global memory once per CTA and not once per field.
+// Each thread owns one (site, field) pair; a warp is 32 consecutive sites of
+// one field, so every pair-chunk load of a neighbour spinor is one contiguous
+// warp access (16 B per thread in FP32).
+//
+// Spin projection in the chiral basis (gamma_k = [[0, i s_k], [-i s_k, 0]],
+// gamma_4 = [[0, 1], [1, 0]]): with upper/lower spin pairs u = (p0, p1),
+// l = (p2, p3),
+//   (1 - gamma_k) p = [h; i s_k h],  h = u - i s_k l,
+//   (1 + gamma_k) p = [h; -i s_k h], h = u + i s_k l,
+//   (1 -/+ gamma_4) p = [h; -/+ h],  h = u -/+ l,
+// so each hop multiplies only a two-spin half spinor by the link.
+// i s_1 (a, b) = (i b, i a);  i s_2 (a, b) = (b, -a);  i s_3 (a, b) = (i a, -i b).
+#include "kernels.h"
+
+namespace dsbcg {
+
+namespace {
+
+template <int P>
+struct SpinorIO;
+
+template <>
+struct SpinorIO<P64> {
+    static __device__ __forceinline__ void load(const double2* f, size_t V, size_t x, double2 p[12], double) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const double2* q = f + ((size_t)c * V + x) * 2;
+            p[2 * c] = __ldg(q);
+            p[2 * c + 1] = __ldg(q + 1);
+        }
+    }
+    static __device__ __forceinline__ void store(double2* f, size_t V, size_t x, const double2 p[12], double) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            double2* q = f + ((size_t)c * V + x) * 2;
+            q[0] = p[2 * c];
+            q[1] = p[2 * c + 1];
+        }
+    }
+};
+
+template <>
+struct SpinorIO<P32> {
+    static __device__ __forceinline__ void load(const float2* f, size_t V, size_t x, float2 p[12], float) {
+        const float4* q = reinterpret_cast<const float4*>(f);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            float4 v = __ldg(q + (size_t)c * V + x);
+            p[2 * c] = make_float2(v.x, v.y);
+            p[2 * c + 1] = make_float2(v.z, v.w);
+        }
+    }
+    static __device__ __forceinline__ void store(float2* f, size_t V, size_t x, const float2 p[12], float) {
+        float4* q = reinterpret_cast<float4*>(f);
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+            q[(size_t)c * V + x] = make_float4(p[2 * c].x, p[2 * c].y, p[2 * c + 1].x, p[2 * c + 1].y);
+    }
+};
+
+template <class H2, class Cvt>
+struct Spinor16 {
+    static __device__ __forceinline__ void load(const H2* f, size_t V, size_t x, float2 p[12], float inv) {
+        const uint2* q = reinterpret_cast<const uint2*>(f);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            uint2 v = __ldg(q + (size_t)c * V + x);
+            const H2* h = reinterpret_cast<const H2*>(&v);
+#pragma unroll
+            for (int w = 0; w < 2; ++w) {
+                float2 t = Cvt::to2(h[w]);
+                p[2 * c + w] = make_float2(t.x * inv, t.y * inv);
+            }
+        }
+    }
+    static __device__ __forceinline__ void store(H2* f, size_t V, size_t x, const float2 p[12], float sc) {
+        uint2* q = reinterpret_cast<uint2*>(f);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            uint2 v;
+            H2* h = reinterpret_cast<H2*>(&v);
+#pragma unroll
+            for (int w = 0; w < 2; ++w)
+                h[w] = Cvt::from2(make_float2(p[2 * c + w].x * sc, p[2 * c + w].y * sc));
+            q[(size_t)c * V + x] = v;
+        }
+    }
+};
+struct CvtBF {
+    static __device__ __forceinline__ float2 to2(__nv_bfloat162 h) { return __bfloat1622float2(h); }
+    static __device__ __forceinline__ __nv_bfloat162 from2(float2 f) { return __float22bfloat162_rn(f); }
+};
+struct CvtH {
+    static __device__ __forceinline__ float2 to2(__half2 h) { return __half22float2(h); }
+    static __device__ __forceinline__ __half2 from2(float2 f) { return __float22half2_rn(f); }
+};
+template <> struct SpinorIO<PBF16> : Spinor16<__nv_bfloat162, CvtBF> {};
+template <> struct SpinorIO<PF16> : Spinor16<__half2, CvtH> {};
+
+template <int P>
+__device__ __forceinline__ typename Tr<P>::C ld_link(const typename Tr<P>::S2* p) {
+    if constexpr (P == P64 || P == P32) {
+        return __ldg(p);
+    } else if constexpr (P == PBF16) {
+        return __bfloat1622float2(*p);
+    } else {
+        return __half22float2(*p);
+    }
+}
+
+// site coordinates and neighbours
+struct Site {
+    int c[4];
+};
+__device__ __forceinline__ Site coords(const Geom& g, int x) {
+    Site s;
+    s.c[0] = x % g.L[0];
+    int r = x / g.L[0];
+    s.c[1] = r % g.L[1];
+    r /= g.L[1];
+    s.c[2] = r % g.L[2];
+    s.c[3] = r / g.L[2];
+    return s;
+}
+__device__ __forceinline__ int stride_of(const Geom& g, int mu) {
+    int st = 1;
+    for (int d = 0; d < mu; ++d) st *= g.L[d];
+    return st;
+}
+// neighbour x + mu (dir = +1) or x - mu (dir = -1); *sign = -1 when the hop
+// crosses the time boundary of an antiperiodic lattice
+__device__ __forceinline__ int neighbour(const Geom& g, int x, const Site& s, int mu, int dir, float* sign) {
+    int st = stride_of(g, mu);
+    int c = s.c[mu];
+    *sign = 1.f;
+    if (dir > 0) {
+        if (c == g.L[mu] - 1) {
+            if (mu == 3 && g.tap) *sign = -1.f;
+            return x - (g.L[mu] - 1) * st;
+        }
+        return x + st;
+    } else {
+        if (c == 0) {
+            if (mu == 3 && g.tap) *sign = -1.f;
+            return x + (g.L[mu] - 1) * st;
+        }
+        return x - st;
+    }
+}
+
+// Uh = U h (fwd) or U^H h (bwd) for the 2 x 3 half spinor h, link in smem
+template <class C>
+__device__ __forceinline__ void su3_mul(const C* __restrict__ u, int stride, const C h[2][3], C out[2][3], bool adj) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int sp = 0; sp < 2; ++sp) out[sp][a] = mk(decltype(h[0][0].x)(0), decltype(h[0][0].x)(0));
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            if (!adj) {
+                C uab = u[(a * 3 + b) * stride];
+#pragma unroll
+                for (int sp = 0; sp < 2; ++sp) cfma(out[sp][a], uab, h[sp][b]);
+            } else {
+                C uba = u[(b * 3 + a) * stride];          // (U^H)_ab = conj(U_ba)
+#pragma unroll
+                for (int sp = 0; sp < 2; ++sp) cfmac(out[sp][a], uba, h[sp][b]);
+            }
+        }
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(512) dslash_kernel(typename Tr<P>::S2* __restrict__ out,
+                                                     const typename Tr<P>::S2* __restrict__ in,
+                                                     size_t ld, const typename Tr<P>::S2* __restrict__ links,
+                                                     Geom g, typename Tr<P>::R kappa, int g5in, int g5out,
+                                                     const Ctl* __restrict__ ctl, int nf_static, float hscale) {
+    using C = typename Tr<P>::C;
+    using R = typename Tr<P>::R;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sl = reinterpret_cast<C*>(smem_raw);          // [8 dirs][9 entries][32 sites]
+
+    int nf = nf_static;
+    if (ctl) {
+        if (ctl->done) return;
+        nf = ctl->mk;
+    }
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int site0 = blockIdx.x * 32;
+    const size_t V = (size_t)g.V;
+
+    // stage the 8 links of each of the 32 sites
+    const int nthr = blockDim.x * blockDim.y;
+    for (int idx = ty * 32 + tx; idx < 8 * 9 * 32; idx += nthr) {
+        int sx = idx & 31;
+        int e = (idx >> 5) % 9;
+        int d = idx / (9 * 32);
+        int x = site0 + sx;
+        C v = mk(R(0), R(0));
+        if (x < g.V) {
+            int mu = d & 3;
+            int src = x;
+            if (d >= 4) {
+                float sg;
+                Site s = coords(g, x);
+                src = neighbour(g, x, s, mu, -1, &sg);
+            }
+            v = ld_link<P>(links + ((size_t)mu * 9 + e) * V + src);
+        }
+        sl[(d * 9 + e) * 32 + sx] = v;
+    }
+    __syncthreads();
+
+    const int x = site0 + tx;
+    if (x >= g.V) return;
+    const R inv = (P == PBF16 || P == PF16) ? R(1) / R(hscale) : R(1);
+    const R scl = (P == PBF16 || P == PF16) ? R(hscale) : R(1);
+    const Site s = coords(g, x);
+    const R g5i = g5in ? R(-1) : R(1);
+
+    for (int f = ty; f < nf; f += blockDim.y) {
+        const typename Tr<P>::S2* fin = in + (size_t)f * ld;
+        C acc[4][3];
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) acc[sp][a] = mk(R(0), R(0));
+
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+#pragma unroll
+            for (int dir = 0; dir < 2; ++dir) {
+                float sgn;
+                int y = neighbour(g, x, s, mu, dir == 0 ? 1 : -1, &sgn);
+                C p[12];
+                SpinorIO<P>::load(fin, V, (size_t)y, p, inv);
+                const R sg = R(sgn);
+                const R su = sg * g5i;          // gamma_5 on input flips the upper spins
+                const R sl_ = sg;
+                C h[2][3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    C u0 = cscale(p[0 * 3 + a], su), u1 = cscale(p[1 * 3 + a], su);
+                    C l0 = cscale(p[2 * 3 + a], sl_), l1 = cscale(p[3 * 3 + a], sl_);
+                    if (dir == 0) {               // forward: (1 - gamma_mu)
+                        if (mu == 0) { h[0][a] = csub(u0, ctimesi(l1)); h[1][a] = csub(u1, ctimesi(l0)); }
+                        if (mu == 1) { h[0][a] = csub(u0, l1); h[1][a] = cadd(u1, l0); }
+                        if (mu == 2) { h[0][a] = csub(u0, ctimesi(l0)); h[1][a] = cadd(u1, ctimesi(l1)); }
+                        if (mu == 3) { h[0][a] = csub(u0, l0); h[1][a] = csub(u1, l1); }
+                    } else {                      // backward: (1 + gamma_mu)
+                        if (mu == 0) { h[0][a] = cadd(u0, ctimesi(l1)); h[1][a] = cadd(u1, ctimesi(l0)); }
+                        if (mu == 1) { h[0][a] = cadd(u0, l1); h[1][a] = csub(u1, l0); }
+                        if (mu == 2) { h[0][a] = cadd(u0, ctimesi(l0)); h[1][a] = csub(u1, ctimesi(l1)); }
+                        if (mu == 3) { h[0][a] = cadd(u0, l0); h[1][a] = cadd(u1, l1); }
+                    }
+                }
+                C uh[2][3];
+                const int d = dir == 0 ? mu : mu + 4;
+                su3_mul(sl + d * 9 * 32 + tx, 32, h, uh, dir != 0);
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    acc[0][a] = cadd(acc[0][a], uh[0][a]);
+                    acc[1][a] = cadd(acc[1][a], uh[1][a]);
+                    C q0 = uh[0][a], q1 = uh[1][a];
+                    if (dir == 0) {               // lower = (i s_k) h, or -h for mu = 4
+                        if (mu == 0) { acc[2][a] = cadd(acc[2][a], ctimesi(q1)); acc[3][a] = cadd(acc[3][a], ctimesi(q0)); }
+                        if (mu == 1) { acc[2][a] = cadd(acc[2][a], q1); acc[3][a] = csub(acc[3][a], q0); }
+                        if (mu == 2) { acc[2][a] = cadd(acc[2][a], ctimesi(q0)); acc[3][a] = csub(acc[3][a], ctimesi(q1)); }
+                        if (mu == 3) { acc[2][a] = csub(acc[2][a], q0); acc[3][a] = csub(acc[3][a], q1); }
+                    } else {                      // lower = -(i s_k) h, or +h for mu = 4
+                        if (mu == 0) { acc[2][a] = csub(acc[2][a], ctimesi(q1)); acc[3][a] = csub(acc[3][a], ctimesi(q0)); }
+                        if (mu == 1) { acc[2][a] = csub(acc[2][a], q1); acc[3][a] = cadd(acc[3][a], q0); }
+                        if (mu == 2) { acc[2][a] = csub(acc[2][a], ctimesi(q0)); acc[3][a] = cadd(acc[3][a], ctimesi(q1)); }
+                        if (mu == 3) { acc[2][a] = cadd(acc[2][a], q0); acc[3][a] = cadd(acc[3][a], q1); }
+                    }
+                }
+            }
+        }
+        C p[12];
+        SpinorIO<P>::load(fin, V, (size_t)x, p, inv);
+        const R go = g5out ? R(-1) : R(1);
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp) {
+            const R sgi = (sp < 2) ? g5i : R(1);
+            const R sgo = (sp < 2) ? go : R(1);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                C v = cscale(p[sp * 3 + a], sgi);
+                v.x = fma(-kappa, acc[sp][a].x, v.x);
+                v.y = fma(-kappa, acc[sp][a].y, v.y);
+                p[sp * 3 + a] = cscale(v, sgo);
+            }
+        }
+        SpinorIO<P>::store(out + (size_t)f * ld, V, (size_t)x, p, scl);
+    }
+}
+
+}  // namespace
+
+void launch_dslash(int prec, void* out, const void* in, size_t ld, const void* links, const Geom& g,
+                   double kappa, int g5in, int g5out, const Ctl* ctl, int nf_static, int nf_max,
+                   float hscale, cudaStream_t st) {
+    int fy = nf_max < 16 ? nf_max : 16;
+    if (fy < 1) fy = 1;
+    dim3 block(32, fy);
+    dim3 grid((g.V + 31) / 32);
+    size_t sm = 8 * 9 * 32 * (prec == P64 ? sizeof(double2) : sizeof(float2));
+    switch (prec) {
+        case P64:
+            dslash_kernel<P64><<<grid, block, sm, st>>>((double2*)out, (const double2*)in, ld,
+                                                         (const double2*)links, g, kappa, g5in, g5out,
+                                                         ctl, nf_static, hscale);
+            break;
+        case P32:
+            dslash_kernel<P32><<<grid, block, sm, st>>>((float2*)out, (const float2*)in, ld,
+                                                         (const float2*)links, g, (float)kappa, g5in,
+                                                         g5out, ctl, nf_static, hscale);
+            break;
+        case PBF16:
+            dslash_kernel<PBF16><<<grid, block, sm, st>>>((__nv_bfloat162*)out, (const __nv_bfloat162*)in, ld,
+                                                           (const __nv_bfloat162*)links, g, (float)kappa,
+                                                           g5in, g5out, ctl, nf_static, hscale);
+            break;
+        case PF16:
+            dslash_kernel<PF16><<<grid, block, sm, st>>>((__half2*)out, (const __half2*)in, ld,
+                                                          (const __half2*)links, g, (float)kappa, g5in,
+                                                          g5out, ctl, nf_static, hscale);
+            break;
+    }
+}
+
+}  // namespace dsbcg

@@ -1,0 +1,95 @@
+// Host-side launchers of the CUDA kernels (one translation unit each), used by
+// the solver and the C ABI in solver.cu.  Field blocks are passed as a base
+// pointer plus a field stride `ld` counted in complex elements; field f of a
+// block starts at base + f * ld.  `prec` is a dsbcg::Prec value.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "common.cuh"
+
+namespace dsbcg {
+
+struct Geom {
+    int L[4];         // Lx, Ly, Lz, Lt
+    int V;            // sites
+    int tap;          // antiperiodic in time
+};
+
+// ---- pack.cu --------------------------------------------------------------
+// canonical complex128 [m][n] (device) <-> internal field block of precision prec
+void launch_pack_fields(int prec, void* dst, size_t ld, const double2* src, int m, size_t V,
+                        float hscale, cudaStream_t st);
+void launch_unpack_fields(int prec, double2* dst, const void* src, size_t ld, int m, size_t V,
+                          float hscale, cudaStream_t st);
+// canonical complex128 [site][4][3][3] -> internal links [mu][9][site]
+void launch_pack_links(int prec, void* dst, const double2* src, size_t V, cudaStream_t st);
+// counts NaN/Inf entries of a complex128 array into *flag (device int)
+void launch_check_finite(const double2* p, size_t count, int* flag, cudaStream_t st);
+// y_f += x_f (FP64 += work precision), fields listed by index arrays on the host
+void launch_accumulate(int prec_x, double2* y, size_t ldy, const void* x, size_t ldx,
+                       int m, size_t n, cudaStream_t st);
+// r_f = b_f - sigma * x_f - ax_f (all FP64), and per-field squared norms (partials)
+void launch_residual(double2* r, const double2* b, const double2* x, const double2* ax,
+                     size_t ld, int m, size_t n, double sigma, double* norm2_partials,
+                     int nblk, cudaStream_t st);
+int residual_blocks(size_t n);
+void launch_reduce_cols(const double* partials, int nblk, int m, double* out, cudaStream_t st);
+
+// ---- dslash.cu ------------------------------------------------------------
+// out_f = D in_f (g5in/g5out wrap it with gamma_5) for fields f < nf,
+// where nf = ctl->mk when ctl != NULL, else nf_static.
+void launch_dslash(int prec, void* out, const void* in, size_t ld, const void* links,
+                   const Geom& g, double kappa, int g5in, int g5out, const Ctl* ctl,
+                   int nf_static, int nf_max, float hscale, cudaStream_t st);
+
+// ---- blas.cu ----------------------------------------------------------------
+int gram_blocks(size_t n, int nf_max);
+// partial sums of X^H Y (nf x nf, FP64) per CTA; herm = 1 computes only the
+// upper triangle of tiles (X == Y); diag_yy = 1 also sums |y_j|^2.
+void launch_gram(int prec, const void* X, const void* Y, size_t ld, size_t n, const Ctl* ctl,
+                 int nf_static, int nf_max, int herm, int diag_yy, double* partials, int nblk,
+                 float hscale, cudaStream_t st);
+size_t gram_partial_doubles(int nf_max);
+// reduce partials -> G (FP64, M_MAX x M_MAX, complex), diag (M_MAX)
+void launch_gram_reduce(const double* partials, int nblk, int nf_max, int herm, int diag_yy,
+                        double2* G, double* diag, const Ctl* ctl, int nf_static,
+                        cudaStream_t st);
+// W = Y - V a - Vp b^H, coefficients from the device (work precision copies)
+void launch_block_update(int prec, void* W, const void* Y, const void* Vk, const void* Vp,
+                         size_t ld, size_t n, const Ctl* ctl, int nf_max,
+                         const void* coef_a, const void* coef_bh, float hscale, cudaStream_t st);
+// V1 = B S (FP64 B, storage-precision V1), S from device (FP64, M_MAX x M_MAX)
+void launch_init_basis(int prec, void* V1, size_t ldv, const double2* B, size_t ldb, size_t n,
+                       const double2* S, const Ctl* ctl, int nf_in, float hscale, cudaStream_t st);
+// fused shift update (kernel (d)): V_{k+1} = W S; for active shifts
+// X_j += P_j Ut_j and P_j <- V_{k+1} - P_j LhT_j
+void launch_shift_update(int prec, int wprec, void* Vnext, const void* W, const void* Vk,
+                         size_t ld, void* P, void* X, size_t ldw, size_t n, int s, int m,
+                         const Ctl* ctl, int nf_max, const void* coefS, const void* coefU,
+                         const void* coefL, const int* active, float hscale, cudaStream_t st);
+
+// ---- small.cu ---------------------------------------------------------------
+struct SmallState;     // device FP64 m x m state, defined in small.cu
+size_t small_state_bytes(int s);
+void launch_small_init(SmallState* ss, Ctl* ctl, const double2* G0, const double* ref, int m,
+                       int s, double dtol, int wprec, void* coefS_w, cudaStream_t st);
+void launch_small_alpha(SmallState* ss, const Ctl* ctl, const double2* alpha, const double* yy,
+                        int wprec, void* coef_a, void* coef_bh, cudaStream_t st);
+void launch_small_qr(SmallState* ss, Ctl* ctl, const double2* G, double dtol, int wprec,
+                     void* coefS_w, cudaStream_t st);
+void launch_small_shift(SmallState* ss, Ctl* ctl, int s, int m, const double* sigma_dev,
+                        const double* target_dev, int freeze, int wprec, void* coefU_w,
+                        void* coefL_w, int* active, int* conv_step, double* res_out,
+                        cudaStream_t st);
+void launch_small_finish(SmallState* ss, Ctl* ctl, int s, const int* active, cudaStream_t st);
+const double2* small_state_S(const SmallState* ss);
+
+// ---- force.cu ---------------------------------------------------------------
+// dU += kappa * w * [F(a, b) + F(c, d)] over nf field pairs (internal FP64/FP32 fields)
+void launch_force(int prec, double2* dU, const void* a, const void* b, const void* c,
+                  const void* d, size_t ld, int nf, const double* w_per_field,
+                  const Geom& g, double kappa, cudaStream_t st);
+
+}  // namespace dsbcg

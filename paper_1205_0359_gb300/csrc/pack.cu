@@ -1,0 +1,197 @@
+// Layout and precision conversion between the canonical ABI layout
+// (complex128, index site*12 + spin*3 + colour) and the internal chunk-major
+// field layout of common.cuh, plus the FP64 vector kernels of the restart
+// loop: true residual r = b - sigma x - A x with its column norms, and
+// x64 += x_work.
+#include "kernels.h"
+
+namespace dsbcg {
+
+namespace {
+
+template <int P>
+__global__ void pack_fields_kernel(typename Tr<P>::S2* __restrict__ dst, size_t ld,
+                                   const double2* __restrict__ src, int m, size_t V, float hscale) {
+    const size_t n = 12 * V;
+    const size_t total = (size_t)m * n;
+    using R = typename Tr<P>::R;
+    const R sc = (P == PBF16 || P == PF16) ? R(hscale) : R(1);
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        size_t f = t / n, i = t % n;                // canonical index i = site*12 + sc
+        size_t x = i / 12;
+        int c = (int)(i % 12);
+        double2 v = src[t];
+        typename Tr<P>::C w = mk(R(v.x), R(v.y));
+        Elem<P>::st(dst + f * ld, fidx<P>(V, x, c), w, sc);
+    }
+}
+
+template <int P>
+__global__ void unpack_fields_kernel(double2* __restrict__ dst, const typename Tr<P>::S2* __restrict__ src,
+                                     size_t ld, int m, size_t V, float hscale) {
+    const size_t n = 12 * V;
+    const size_t total = (size_t)m * n;
+    using R = typename Tr<P>::R;
+    const R inv = (P == PBF16 || P == PF16) ? R(1) / R(hscale) : R(1);
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        size_t f = t / n, i = t % n;
+        size_t x = i / 12;
+        int c = (int)(i % 12);
+        typename Tr<P>::C w = Elem<P>::ld(src + f * ld, fidx<P>(V, x, c), inv);
+        dst[t] = make_double2((double)w.x, (double)w.y);
+    }
+}
+
+template <int P>
+__global__ void pack_links_kernel(typename Tr<P>::S2* __restrict__ dst, const double2* __restrict__ src, size_t V) {
+    const size_t total = V * 36;
+    using R = typename Tr<P>::R;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        size_t x = t / 36;
+        int r = (int)(t % 36);
+        int mu = r / 9, e = r % 9;
+        double2 v = src[t];
+        Elem<P>::st(dst, ((size_t)mu * 9 + e) * V + x, mk(R(v.x), R(v.y)), R(1));
+    }
+}
+
+__global__ void check_finite_kernel(const double2* __restrict__ p, size_t count, int* flag) {
+    int bad = 0;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count;
+         t += (size_t)gridDim.x * blockDim.x) {
+        double2 v = p[t];
+        if (!isfinite(v.x) || !isfinite(v.y)) bad = 1;
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+template <int PX>
+__global__ void accumulate_kernel(double2* __restrict__ y, size_t ldy, const typename Tr<PX>::S2* __restrict__ x,
+                                  size_t ldx, int m, size_t n) {
+    const size_t total = (size_t)m * n;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        size_t f = t / n, i = t % n;
+        typename Tr<PX>::C v = Elem<PX>::ld(x + f * ldx, i, 1);
+        double2 a = y[f * ldy + i];
+        a.x += (double)v.x;
+        a.y += (double)v.y;
+        y[f * ldy + i] = a;
+    }
+}
+
+constexpr int RES_THREADS = 256;
+
+// one block column per field: grid (nblk, m)
+__global__ void residual_kernel(double2* __restrict__ r, const double2* __restrict__ b,
+                                const double2* __restrict__ x, const double2* __restrict__ ax, size_t ld,
+                                size_t n, double sigma, double* __restrict__ partials, int nblk) {
+    const int f = blockIdx.y;
+    const size_t off = (size_t)f * ld;
+    double acc = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)nblk * blockDim.x) {
+        double2 bb = b[off + i], xx = x[off + i], aa = ax[off + i];
+        double2 rr = make_double2(bb.x - sigma * xx.x - aa.x, bb.y - sigma * xx.y - aa.y);
+        r[off + i] = rr;
+        acc += rr.x * rr.x + rr.y * rr.y;
+    }
+    __shared__ double red[RES_THREADS / 32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < RES_THREADS / 32 ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) partials[(size_t)f * nblk + blockIdx.x] = v;
+    }
+}
+
+// out[f] = sum_b partials[f * nblk + b], fixed order
+__global__ void reduce_cols_kernel(const double* __restrict__ partials, int nblk, double* __restrict__ out) {
+    const int f = blockIdx.x;
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc += partials[(size_t)f * nblk + b];
+    __shared__ double red[8];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
+        out[f] = v;
+    }
+}
+
+inline int grid_for(size_t total) {
+    size_t g = (total + 255) / 256;
+    if (g > 152 * 16) g = 152 * 16;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace
+
+void launch_pack_fields(int prec, void* dst, size_t ld, const double2* src, int m, size_t V, float hscale,
+                        cudaStream_t st) {
+    int g = grid_for((size_t)m * 12 * V);
+    switch (prec) {
+        case P64: pack_fields_kernel<P64><<<g, 256, 0, st>>>((double2*)dst, ld, src, m, V, hscale); break;
+        case P32: pack_fields_kernel<P32><<<g, 256, 0, st>>>((float2*)dst, ld, src, m, V, hscale); break;
+        case PBF16: pack_fields_kernel<PBF16><<<g, 256, 0, st>>>((__nv_bfloat162*)dst, ld, src, m, V, hscale); break;
+        case PF16: pack_fields_kernel<PF16><<<g, 256, 0, st>>>((__half2*)dst, ld, src, m, V, hscale); break;
+    }
+}
+
+void launch_unpack_fields(int prec, double2* dst, const void* src, size_t ld, int m, size_t V, float hscale,
+                          cudaStream_t st) {
+    int g = grid_for((size_t)m * 12 * V);
+    switch (prec) {
+        case P64: unpack_fields_kernel<P64><<<g, 256, 0, st>>>(dst, (const double2*)src, ld, m, V, hscale); break;
+        case P32: unpack_fields_kernel<P32><<<g, 256, 0, st>>>(dst, (const float2*)src, ld, m, V, hscale); break;
+        case PBF16: unpack_fields_kernel<PBF16><<<g, 256, 0, st>>>(dst, (const __nv_bfloat162*)src, ld, m, V, hscale); break;
+        case PF16: unpack_fields_kernel<PF16><<<g, 256, 0, st>>>(dst, (const __half2*)src, ld, m, V, hscale); break;
+    }
+}
+
+void launch_pack_links(int prec, void* dst, const double2* src, size_t V, cudaStream_t st) {
+    int g = grid_for(V * 36);
+    switch (prec) {
+        case P64: pack_links_kernel<P64><<<g, 256, 0, st>>>((double2*)dst, src, V); break;
+        case P32: pack_links_kernel<P32><<<g, 256, 0, st>>>((float2*)dst, src, V); break;
+        case PBF16: pack_links_kernel<PBF16><<<g, 256, 0, st>>>((__nv_bfloat162*)dst, src, V); break;
+        case PF16: pack_links_kernel<PF16><<<g, 256, 0, st>>>((__half2*)dst, src, V); break;
+    }
+}
+
+void launch_check_finite(const double2* p, size_t count, int* flag, cudaStream_t st) {
+    check_finite_kernel<<<grid_for(count), 256, 0, st>>>(p, count, flag);
+}
+
+void launch_accumulate(int prec_x, double2* y, size_t ldy, const void* x, size_t ldx, int m, size_t n,
+                       cudaStream_t st) {
+    int g = grid_for((size_t)m * n);
+    if (prec_x == P64)
+        accumulate_kernel<P64><<<g, 256, 0, st>>>(y, ldy, (const double2*)x, ldx, m, n);
+    else
+        accumulate_kernel<P32><<<g, 256, 0, st>>>(y, ldy, (const float2*)x, ldx, m, n);
+}
+
+int residual_blocks(size_t n) {
+    size_t b = (n + RES_THREADS - 1) / RES_THREADS;
+    return (int)(b < 304 ? (b < 1 ? 1 : b) : 304);
+}
+
+void launch_residual(double2* r, const double2* b, const double2* x, const double2* ax, size_t ld, int m,
+                     size_t n, double sigma, double* partials, int nblk, cudaStream_t st) {
+    dim3 grid(nblk, m);
+    residual_kernel<<<grid, RES_THREADS, 0, st>>>(r, b, x, ax, ld, n, sigma, partials, nblk);
+}
+
+void launch_reduce_cols(const double* partials, int nblk, int m, double* out, cudaStream_t st) {
+    reduce_cols_kernel<<<m, 256, 0, st>>>(partials, nblk, out);
+}
+
+}  // namespace dsbcg

@@ -1,0 +1,792 @@
+// Host orchestration and the C ABI (include/dsbcg.h).
+//
+// A solve (Sec. 3) runs as:
+//   1. pack B into the internal FP64 layout; ||b_i||;
+//   2. joint inner solve: the block Lanczos process of A seeded with B, and
+//      every shift's block root-free Cholesky recurrences, in the storage
+//      precision (FP32 arithmetic for FP32/BF16/FP16 storage, FP64 for FP64);
+//      each block step is a fixed sequence of kernels that read the block
+//      widths and the convergence state from a device-resident control block,
+//      so the host enqueues steps without synchronising and only polls the
+//      `done` flag every `poll_every` steps;
+//   3. FP64 true residuals r_ij = b_i - (sigma_j + A) x_ij (reliable update);
+//   4. every shift with a residual above tol is restarted on its own true
+//      residual (block CG on sigma_j I + A, same kernels with s = 1) and its
+//      FP64 solution corrected, until every ||r_ij|| <= tol ||b_i|| or the
+//      restart cap is reached.
+// The paper's own code runs in FP64 only (Sec. 4); the reduced-precision
+// inner iteration with FP64 true-residual restarts is a GB300-specific
+// addition.  Restarting is valid because the Galerkin iterate of a restarted
+// process is again of the form of Eq. 3.2 for the new right-hand side.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
+#include "../../include/dsbcg.h"
+#include "kernels.h"
+
+using namespace dsbcg;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct KEvent {
+    int cls;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct dsbcg_ctx {
+    Geom g;
+    size_t V = 0, n = 0, ld = 0;
+    double kappa = 0;
+    cudaStream_t st = nullptr;
+    double2* gauge64 = nullptr;          // canonical copy of the links (device)
+    void* links[4] = {nullptr, nullptr, nullptr, nullptr};
+    float hscale = 1.f;
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<KEvent> ev_live;
+    double kms[8] = {0};
+    long long klaunch[8] = {0};
+    // workspace
+    std::vector<void*> allocs;
+    struct WS {
+        int m = 0, s = 0, prec = -1;
+        void *vring = nullptr, *zw = nullptr, *y = nullptr;       // storage precision
+        void *P = nullptr, *Xin = nullptr;                        // work precision
+        double2 *B64 = nullptr, *X64 = nullptr, *R64 = nullptr, *T64a = nullptr, *T64b = nullptr, *rhs = nullptr;
+        double* partials = nullptr;
+        double* rpart = nullptr;
+        SmallState* ss = nullptr;
+        Ctl* ctl = nullptr;
+        double2 *G = nullptr, *alpha = nullptr;
+        double *diag = nullptr, *yy = nullptr;
+        void *coef_a = nullptr, *coef_bh = nullptr, *coefS = nullptr, *coefU = nullptr, *coefL = nullptr;
+        int *active = nullptr, *conv_step = nullptr;
+        double *res = nullptr, *sigma = nullptr, *target = nullptr, *norms = nullptr;
+        int* flag = nullptr;
+        Ctl* h_ctl = nullptr;            // pinned
+        double* h_norms = nullptr;       // pinned
+        int* h_conv = nullptr;           // pinned
+        int nblk = 0, rblk = 0;
+        std::vector<void*> mem;
+    } ws;
+};
+
+namespace {
+
+#define CK(x)                                              \
+    do {                                                   \
+        cudaError_t e_ = (x);                              \
+        if (e_ != cudaSuccess) {                           \
+            fprintf(stderr, "dsbcg: CUDA error %s at %s:%d\n", cudaGetErrorString(e_), __FILE__, __LINE__); \
+            return e_ == cudaErrorMemoryAllocation ? DSBCG_ERR_OOM : DSBCG_ERR_CUDA; \
+        }                                                  \
+    } while (0)
+
+#define CKS(x)                                    \
+    do {                                          \
+        dsbcg_status s_ = (x);                    \
+        if (s_ != DSBCG_OK) return s_;            \
+    } while (0)
+
+inline int work_prec(int p) { return p == P64 ? P64 : P32; }
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+dsbcg_status dmalloc(dsbcg_ctx* c, void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return DSBCG_ERR_OOM;
+    }
+    c->ws.mem.push_back(*p);
+    return DSBCG_OK;
+}
+
+void free_ws(dsbcg_ctx* c) {
+    cudaStreamSynchronize(c->st);
+    for (void* p : c->ws.mem) cudaFree(p);
+    c->ws.mem.clear();
+    if (c->ws.h_ctl) cudaFreeHost(c->ws.h_ctl);
+    if (c->ws.h_norms) cudaFreeHost(c->ws.h_norms);
+    if (c->ws.h_conv) cudaFreeHost(c->ws.h_conv);
+    c->ws = dsbcg_ctx::WS();
+}
+
+size_t prec_elem_bytes(int p) { return (size_t)prec_bytes(p); }
+
+dsbcg_status ensure_links(dsbcg_ctx* c, int prec) {
+    if (c->links[prec]) return DSBCG_OK;
+    void* p = nullptr;
+    CK(cudaMalloc(&p, c->V * 36 * prec_elem_bytes(prec)));
+    launch_pack_links(prec, p, c->gauge64, c->V, c->st);
+    CK(cudaGetLastError());
+    c->links[prec] = p;
+    return DSBCG_OK;
+}
+
+dsbcg_status ensure_ws(dsbcg_ctx* c, int m, int s, int prec) {
+    auto& w = c->ws;
+    if (w.prec == prec && w.m >= m && w.s >= s && w.m == m) return DSBCG_OK;
+    free_ws(c);
+    const size_t ld = c->ld, n = c->n;
+    const size_t fb = prec_elem_bytes(prec) * ld;           // storage field bytes
+    const size_t wb = prec_elem_bytes(work_prec(prec)) * ld; // work field bytes
+    const size_t db = sizeof(double2) * ld;
+    (void)n;
+    CKS(dmalloc(c, &w.vring, 2 * m * fb));
+    CKS(dmalloc(c, &w.zw, m * fb));
+    CKS(dmalloc(c, &w.y, m * fb));
+    CKS(dmalloc(c, (void**)&w.P, (size_t)s * m * wb));
+    CKS(dmalloc(c, (void**)&w.Xin, (size_t)s * m * wb));
+    CKS(dmalloc(c, (void**)&w.B64, m * db));
+    CKS(dmalloc(c, (void**)&w.X64, (size_t)s * m * db));
+    CKS(dmalloc(c, (void**)&w.R64, m * db));
+    CKS(dmalloc(c, (void**)&w.T64a, m * db));
+    CKS(dmalloc(c, (void**)&w.T64b, m * db));
+    CKS(dmalloc(c, (void**)&w.rhs, m * db));
+    w.nblk = gram_blocks(c->n, m);
+    CKS(dmalloc(c, (void**)&w.partials, gram_partial_doubles(M_MAX) * sizeof(double)));
+    w.rblk = residual_blocks(c->n);
+    CKS(dmalloc(c, (void**)&w.rpart, (size_t)w.rblk * m * sizeof(double)));
+    CKS(dmalloc(c, (void**)&w.ss, small_state_bytes(s)));
+    CKS(dmalloc(c, (void**)&w.ctl, sizeof(Ctl)));
+    CKS(dmalloc(c, (void**)&w.G, M_MAX * M_MAX * sizeof(double2)));
+    CKS(dmalloc(c, (void**)&w.alpha, M_MAX * M_MAX * sizeof(double2)));
+    CKS(dmalloc(c, (void**)&w.diag, M_MAX * sizeof(double)));
+    CKS(dmalloc(c, (void**)&w.yy, M_MAX * sizeof(double)));
+    const size_t tb = M_MAX * M_MAX * sizeof(double2);
+    CKS(dmalloc(c, &w.coef_a, tb));
+    CKS(dmalloc(c, &w.coef_bh, tb));
+    CKS(dmalloc(c, &w.coefS, tb));
+    CKS(dmalloc(c, &w.coefU, (size_t)s * tb));
+    CKS(dmalloc(c, &w.coefL, (size_t)s * tb));
+    CKS(dmalloc(c, (void**)&w.active, s * sizeof(int)));
+    CKS(dmalloc(c, (void**)&w.conv_step, (size_t)s * m * sizeof(int)));
+    CKS(dmalloc(c, (void**)&w.res, (size_t)s * m * sizeof(double)));
+    CKS(dmalloc(c, (void**)&w.sigma, s * sizeof(double)));
+    CKS(dmalloc(c, (void**)&w.target, (size_t)s * m * sizeof(double)));
+    CKS(dmalloc(c, (void**)&w.norms, (size_t)(s + 1) * m * sizeof(double)));
+    CKS(dmalloc(c, (void**)&w.flag, sizeof(int)));
+    CK(cudaMallocHost((void**)&w.h_ctl, sizeof(Ctl)));
+    CK(cudaMallocHost((void**)&w.h_norms, (size_t)(s + 1) * m * sizeof(double)));
+    CK(cudaMallocHost((void**)&w.h_conv, (size_t)s * m * sizeof(int)));
+    w.m = m;
+    w.s = s;
+    w.prec = prec;
+    return DSBCG_OK;
+}
+
+// ---- profiling -------------------------------------------------------------
+cudaEvent_t ev_get(dsbcg_ctx* c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+struct Prof {
+    dsbcg_ctx* c;
+    int cls;
+    cudaEvent_t a = nullptr;
+    Prof(dsbcg_ctx* c_, int cls_) : c(c_), cls(cls_) {
+        if (c->profiling) {
+            a = ev_get(c);
+            cudaEventRecord(a, c->st);
+        }
+        c->klaunch[cls] += 1;
+    }
+    ~Prof() {
+        if (c->profiling) {
+            cudaEvent_t b = ev_get(c);
+            cudaEventRecord(b, c->st);
+            c->ev_live.push_back({cls, a, b});
+        }
+    }
+};
+void prof_collect(dsbcg_ctx* c) {
+    // caller has synchronised the stream
+    for (auto& k : c->ev_live) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, k.a, k.b);
+        c->kms[k.cls] += ms;
+        c->ev_pool.push_back(k.a);
+        c->ev_pool.push_back(k.b);
+    }
+    c->ev_live.clear();
+}
+
+// ---- FP64 operator on internal FP64 fields ----------------------------------
+// out = A in for nf FP64 fields (tmp receives D in)
+void apply_A64(dsbcg_ctx* c, double2* out, const double2* in, double2* tmp, int nf) {
+    {
+        Prof p(c, DSBCG_KCLASS_RESIDUAL);
+        launch_dslash(P64, tmp, in, c->ld, c->links[P64], c->g, c->kappa, 0, 0, nullptr, nf, nf, 1.f, c->st);
+    }
+    {
+        Prof p(c, DSBCG_KCLASS_RESIDUAL);
+        launch_dslash(P64, out, tmp, c->ld, c->links[P64], c->g, c->kappa, 1, 1, nullptr, nf, nf, 1.f, c->st);
+    }
+}
+
+// r = b - sigma x - A x for m FP64 fields; squared column norms into h_out (host)
+dsbcg_status true_residual(dsbcg_ctx* c, double2* r, const double2* b, const double2* x, int m, double sigma,
+                           double* h_out) {
+    auto& w = c->ws;
+    apply_A64(c, w.T64b, x, w.T64a, m);
+    {
+        Prof p(c, DSBCG_KCLASS_RESIDUAL);
+        launch_residual(r, b, x, w.T64b, c->ld, m, c->n, sigma, w.rpart, w.rblk, c->st);
+    }
+    launch_reduce_cols(w.rpart, w.rblk, m, w.norms, c->st);
+    CK(cudaMemcpyAsync(w.h_norms, w.norms, m * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    for (int i = 0; i < m; ++i) h_out[i] = w.h_norms[i];
+    return DSBCG_OK;
+}
+
+struct InnerResult {
+    int steps = 0;
+    long long mvms = 0;
+    int deflations = 0;
+    int final_rank = 0;
+    int status = 0;
+    bool converged = false;
+};
+
+// Joint inner solve on the FP64 right-hand sides `rhs` (m_in fields, internal
+// layout): for the shifts sig[0..s_in), X_in[j] (work precision) receives the
+// iterate, targets are absolute residual norms per (j, i).
+dsbcg_status inner_solve(dsbcg_ctx* c, const double2* rhs, int m_in, const double* sig, int s_in,
+                         const double* targets, int prec, double dtol, int max_steps, int freeze, int poll_every,
+                         InnerResult* out, int step_offset, int* conv_step_host) {
+    auto& w = c->ws;
+    const int wp = work_prec(prec);
+    const size_t ld = c->ld, n = c->n;
+    const size_t fb = prec_elem_bytes(prec) * ld;
+    const size_t wb = prec_elem_bytes(wp) * ld;
+    CK(cudaMemcpyAsync(w.sigma, sig, s_in * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemcpyAsync(w.target, targets, (size_t)s_in * m_in * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    CK(cudaMemsetAsync(w.conv_step, 0xff, (size_t)s_in * m_in * sizeof(int), c->st));
+    CK(cudaMemsetAsync(w.Xin, 0, (size_t)s_in * m_in * wb, c->st));
+    // a0: G0 = B^H B (FP64), pivoted Cholesky with deflation, V_1 = B S0
+    {
+        Prof p(c, DSBCG_KCLASS_GRAM);
+        launch_gram(P64, rhs, rhs, ld, n, nullptr, m_in, m_in, 1, 1, w.partials, w.nblk, 1.f, c->st);
+    }
+    launch_gram_reduce(w.partials, w.nblk, m_in, 1, 1, w.G, w.diag, nullptr, m_in, c->st);
+    {
+        Prof p(c, DSBCG_KCLASS_SMALL);
+        launch_small_init(w.ss, w.ctl, w.G, w.diag, m_in, s_in, dtol, wp, w.coefS, c->st);
+    }
+    char* ring = (char*)w.vring;
+    launch_init_basis(prec, ring + 1 * (size_t)m_in * fb, ld, rhs, ld, n, small_state_S(w.ss), w.ctl, m_in,
+                      c->hscale, c->st);
+    CK(cudaGetLastError());
+    // block steps
+    int step = 0;
+    bool done = false;
+    while (!done) {
+        for (int q = 0; q < poll_every && step < max_steps; ++q) {
+            ++step;
+            void* Vk = ring + (size_t)(step % 2) * m_in * fb;
+            void* Vo = ring + (size_t)((step + 1) % 2) * m_in * fb;     // V_{k-1}, then V_{k+1}
+            {
+                Prof p(c, DSBCG_KCLASS_DSLASH);
+                launch_dslash(prec, w.zw, Vk, ld, c->links[prec], c->g, c->kappa, 0, 0, w.ctl, 0, m_in, c->hscale,
+                              c->st);
+            }
+            {
+                Prof p(c, DSBCG_KCLASS_DSLASH);
+                launch_dslash(prec, w.y, w.zw, ld, c->links[prec], c->g, c->kappa, 1, 1, w.ctl, 0, m_in,
+                              c->hscale, c->st);
+            }
+            {
+                Prof p(c, DSBCG_KCLASS_GRAM);
+                launch_gram(prec, Vk, w.y, ld, n, w.ctl, 0, m_in, 0, 1, w.partials, w.nblk, c->hscale, c->st);
+            }
+            {
+                Prof p(c, DSBCG_KCLASS_SMALL);
+                launch_gram_reduce(w.partials, w.nblk, m_in, 0, 1, w.alpha, w.yy, w.ctl, 0, c->st);
+                launch_small_alpha(w.ss, w.ctl, w.alpha, w.yy, wp, w.coef_a, w.coef_bh, c->st);
+            }
+            {
+                Prof p(c, DSBCG_KCLASS_UPDATE);
+                launch_block_update(prec, w.zw, w.y, Vk, Vo, ld, n, w.ctl, m_in, w.coef_a, w.coef_bh, c->hscale,
+                                    c->st);
+            }
+            {
+                Prof p(c, DSBCG_KCLASS_GRAM);
+                launch_gram(prec, w.zw, w.zw, ld, n, w.ctl, 0, m_in, 1, 0, w.partials, w.nblk, c->hscale, c->st);
+            }
+            {
+                Prof p(c, DSBCG_KCLASS_SMALL);
+                launch_gram_reduce(w.partials, w.nblk, m_in, 1, 0, w.G, w.diag, w.ctl, 0, c->st);
+                launch_small_qr(w.ss, w.ctl, w.G, dtol, wp, w.coefS, c->st);
+                launch_small_shift(w.ss, w.ctl, s_in, m_in, w.sigma, w.target, freeze, wp, w.coefU, w.coefL,
+                                   w.active, w.conv_step, w.res, c->st);
+            }
+            {
+                Prof p(c, DSBCG_KCLASS_SHIFT);
+                launch_shift_update(prec, wp, Vo, w.zw, Vk, ld, w.P, w.Xin, ld, n, s_in, m_in, w.ctl, m_in, w.coefS,
+                                    w.coefU, w.coefL, w.active, c->hscale, c->st);
+            }
+            {
+                Prof p(c, DSBCG_KCLASS_SMALL);
+                launch_small_finish(w.ss, w.ctl, s_in, w.active, c->st);
+            }
+        }
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(w.h_ctl, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        prof_collect(c);
+        if (w.h_ctl->done || w.h_ctl->status != 0 || step >= max_steps) done = true;
+    }
+    (void)wb;
+    CK(cudaMemcpyAsync(w.h_conv, w.conv_step, (size_t)s_in * m_in * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    if (conv_step_host) {
+        for (int t = 0; t < s_in * m_in; ++t)
+            conv_step_host[t] = w.h_conv[t] >= 0 ? w.h_conv[t] + step_offset : -1;
+    }
+    const Ctl& h = *w.h_ctl;
+    out->steps = h.last_step;
+    out->mvms = h.mvms;
+    out->deflations = h.deflations;
+    out->final_rank = h.mk;
+    out->status = h.status;
+    out->converged = h.done && h.status == 0;
+    return DSBCG_OK;
+}
+
+double default_dtol(int prec) {
+    switch (prec) {
+        case P64: return 1e-7;
+        case P32: return 1e-3;
+        case PF16: return 1e-2;
+        default: return 3e-2;
+    }
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+void dsbcg_params_default(dsbcg_params* p) {
+    if (!p) return;
+    p->storage = DSBCG_PREC_FP32;
+    p->dtol = 0.0;
+    p->max_block_steps = 100000;
+    p->max_restarts = 50;
+    p->restart_drop = 1e-6;
+    p->poll_every = 16;
+    p->freeze_converged = 1;
+    p->refine = 1;
+}
+
+const char* dsbcg_error_string(dsbcg_status s) {
+    switch (s) {
+        case DSBCG_OK: return "ok";
+        case DSBCG_NOT_CONVERGED: return "not converged (iteration or restart cap reached)";
+        case DSBCG_ERR_ARG: return "invalid argument";
+        case DSBCG_ERR_NOT_HPD: return "sigma_j I + T is not hermitian positive definite";
+        case DSBCG_ERR_CUDA: return "CUDA runtime error";
+        case DSBCG_ERR_OOM: return "device out of memory";
+        case DSBCG_ERR_NONFINITE: return "non-finite input";
+        case DSBCG_ERR_UNSUPPORTED: return "unsupported option";
+    }
+    return "unknown status";
+}
+
+const char* dsbcg_version(void) { return "dsbcg 0.1 sm_103a"; }
+
+dsbcg_status dsbcg_create(dsbcg_ctx** out, const int dims[4], const void* gauge, double kappa, int t_antiperiodic,
+                          void* stream) {
+    if (!out || !dims || !gauge) return DSBCG_ERR_ARG;
+    *out = nullptr;
+    for (int d = 0; d < 4; ++d)
+        if (dims[d] < 2 || dims[d] > 4096) return DSBCG_ERR_ARG;
+    if (!(kappa == kappa) || !isfinite(kappa)) return DSBCG_ERR_ARG;
+    size_t V = (size_t)dims[0] * dims[1] * dims[2] * dims[3];
+    if (V > (size_t)1 << 30) return DSBCG_ERR_ARG;
+    dsbcg_ctx* c = new dsbcg_ctx();
+    for (int d = 0; d < 4; ++d) c->g.L[d] = dims[d];
+    c->g.V = (int)V;
+    c->g.tap = t_antiperiodic ? 1 : 0;
+    c->V = V;
+    c->n = 12 * V;
+    c->ld = (c->n + 127) / 128 * 128;
+    c->kappa = kappa;
+    c->st = (cudaStream_t)stream;
+    // 16-bit scale: power of two near sqrt(n)
+    c->hscale = (float)ldexp(1.0, (int)lround(0.5 * log2((double)c->n)));
+    dsbcg_status st = dsbcg_update_gauge(c, gauge);
+    if (st != DSBCG_OK) {
+        dsbcg_destroy(c);
+        return st;
+    }
+    *out = c;
+    return DSBCG_OK;
+}
+
+dsbcg_status dsbcg_update_gauge(dsbcg_ctx* c, const void* gauge) {
+    if (!c || !gauge) return DSBCG_ERR_ARG;
+    const size_t bytes = c->V * 36 * sizeof(double2);
+    if (!c->gauge64) CK(cudaMalloc((void**)&c->gauge64, bytes));
+    CK(cudaMemcpyAsync(c->gauge64, gauge, bytes, is_device_ptr(gauge) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       c->st));
+    int* flag = nullptr;
+    CK(cudaMalloc((void**)&flag, sizeof(int)));
+    cudaMemsetAsync(flag, 0, sizeof(int), c->st);
+    launch_check_finite(c->gauge64, c->V * 36, flag, c->st);
+    int h = 0;
+    cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+    CK(cudaStreamSynchronize(c->st));
+    cudaFree(flag);
+    if (h) return DSBCG_ERR_NONFINITE;
+    for (int p = 0; p < 4; ++p) {
+        if (c->links[p]) {
+            cudaFree(c->links[p]);
+            c->links[p] = nullptr;
+        }
+    }
+    CKS(ensure_links(c, P64));
+    return DSBCG_OK;
+}
+
+void dsbcg_destroy(dsbcg_ctx* c) {
+    if (!c) return;
+    free_ws(c);
+    for (int p = 0; p < 4; ++p)
+        if (c->links[p]) cudaFree(c->links[p]);
+    if (c->gauge64) cudaFree(c->gauge64);
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    for (auto& k : c->ev_live) {
+        cudaEventDestroy(k.a);
+        cudaEventDestroy(k.b);
+    }
+    delete c;
+}
+
+dsbcg_status dsbcg_set_profiling(dsbcg_ctx* c, int on) {
+    if (!c) return DSBCG_ERR_ARG;
+    c->profiling = on != 0;
+    return DSBCG_OK;
+}
+
+dsbcg_status dsbcg_apply(dsbcg_ctx* c, int op, int storage, int m, const void* in, void* out) {
+    if (!c || !in || !out || m < 1 || m > 4096 || op < 0 || op > 2 || storage < 0 || storage > 3)
+        return DSBCG_ERR_ARG;
+    CKS(ensure_links(c, storage));
+    const size_t n = c->n, ld = c->ld;
+    const size_t fb = prec_elem_bytes(storage) * ld;
+    void *a = nullptr, *b = nullptr, *t = nullptr;
+    double2 *din = nullptr, *dout = nullptr;
+    const bool in_dev = is_device_ptr(in), out_dev = is_device_ptr(out);
+    dsbcg_status rs = DSBCG_OK;
+    auto fail = [&](dsbcg_status s) { rs = s; };
+    if (cudaMalloc(&a, m * fb) != cudaSuccess || cudaMalloc(&b, m * fb) != cudaSuccess ||
+        cudaMalloc(&t, m * fb) != cudaSuccess) {
+        fail(DSBCG_ERR_OOM);
+    }
+    if (rs == DSBCG_OK && !in_dev) {
+        if (cudaMalloc((void**)&din, m * n * sizeof(double2)) != cudaSuccess) fail(DSBCG_ERR_OOM);
+        else cudaMemcpyAsync(din, in, m * n * sizeof(double2), cudaMemcpyHostToDevice, c->st);
+    }
+    if (rs == DSBCG_OK && !out_dev) {
+        if (cudaMalloc((void**)&dout, m * n * sizeof(double2)) != cudaSuccess) fail(DSBCG_ERR_OOM);
+    }
+    if (rs == DSBCG_OK) {
+        const double2* src = in_dev ? (const double2*)in : din;
+        double2* dst = out_dev ? (double2*)out : dout;
+        launch_pack_fields(storage, a, ld, src, m, c->V, c->hscale, c->st);
+        if (op == DSBCG_OP_D) {
+            Prof p(c, DSBCG_KCLASS_DSLASH);
+            launch_dslash(storage, b, a, ld, c->links[storage], c->g, c->kappa, 0, 0, nullptr, m, m, c->hscale, c->st);
+        } else if (op == DSBCG_OP_DDAG) {
+            Prof p(c, DSBCG_KCLASS_DSLASH);
+            launch_dslash(storage, b, a, ld, c->links[storage], c->g, c->kappa, 1, 1, nullptr, m, m, c->hscale, c->st);
+        } else {
+            {
+                Prof p(c, DSBCG_KCLASS_DSLASH);
+                launch_dslash(storage, t, a, ld, c->links[storage], c->g, c->kappa, 0, 0, nullptr, m, m, c->hscale,
+                              c->st);
+            }
+            Prof p(c, DSBCG_KCLASS_DSLASH);
+            launch_dslash(storage, b, t, ld, c->links[storage], c->g, c->kappa, 1, 1, nullptr, m, m, c->hscale, c->st);
+        }
+        launch_unpack_fields(storage, dst, b, ld, m, c->V, c->hscale, c->st);
+        if (!out_dev) cudaMemcpyAsync(out, dout, m * n * sizeof(double2), cudaMemcpyDeviceToHost, c->st);
+        if (cudaGetLastError() != cudaSuccess) fail(DSBCG_ERR_CUDA);
+        if (cudaStreamSynchronize(c->st) != cudaSuccess) fail(DSBCG_ERR_CUDA);
+        prof_collect(c);
+    }
+    cudaFree(a);
+    cudaFree(b);
+    cudaFree(t);
+    if (din) cudaFree(din);
+    if (dout) cudaFree(dout);
+    return rs;
+}
+
+dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double* sigma, double tol,
+                         const dsbcg_params* params, void* X, dsbcg_stats* stats) {
+    auto t0 = std::chrono::steady_clock::now();
+    if (!c || !B || !X || !sigma || m < 1 || m > M_MAX || s < 1 || s > S_MAX) return DSBCG_ERR_ARG;
+    if (!(tol >= 0.0) || !isfinite(tol)) return DSBCG_ERR_ARG;
+    for (int j = 0; j < s; ++j)
+        if (!(sigma[j] >= 0.0) || !isfinite(sigma[j])) return DSBCG_ERR_ARG;
+    dsbcg_params prm;
+    if (params) prm = *params;
+    else dsbcg_params_default(&prm);
+    const int prec = prm.storage;
+    if (prec < 0 || prec > 3) return DSBCG_ERR_ARG;
+    if (prm.poll_every < 1) prm.poll_every = 1;
+    const double dtol = prm.dtol > 0 ? prm.dtol : default_dtol(prec);
+    CKS(ensure_links(c, prec));
+    CKS(ensure_links(c, P64));
+    CKS(ensure_ws(c, m, s, prec));
+    auto& w = c->ws;
+    const size_t n = c->n, ld = c->ld;
+    const size_t db = ld * sizeof(double2);
+    for (int q = 0; q < 8; ++q) {
+        c->kms[q] = 0;
+        c->klaunch[q] = 0;
+    }
+
+    // --- inputs: B -> internal FP64 (staging through X64's storage if on the host)
+    const bool b_dev = is_device_ptr(B), x_dev = is_device_ptr(X);
+    double2* bcanon = nullptr;
+    if (b_dev) {
+        bcanon = (double2*)B;
+    } else {
+        bcanon = w.X64;        // X64 has >= m*ld complex; used as staging before it is zeroed
+        CK(cudaMemcpyAsync(bcanon, B, (size_t)m * n * sizeof(double2), cudaMemcpyHostToDevice, c->st));
+    }
+    CK(cudaMemsetAsync(w.flag, 0, sizeof(int), c->st));
+    launch_check_finite(bcanon, (size_t)m * n, w.flag, c->st);
+    launch_pack_fields(P64, w.B64, ld, bcanon, m, c->V, 1.f, c->st);
+    int hflag = 0;
+    CK(cudaMemcpyAsync(&hflag, w.flag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaMemsetAsync(w.X64, 0, (size_t)s * m * db, c->st));
+    // ||b_i||^2 via the residual kernel with x = 0 (A 0 = 0)
+    std::vector<double> bn2(m), bn(m);
+    {
+        launch_residual(w.R64, w.B64, w.X64, w.X64, ld, m, n, 0.0, w.rpart, w.rblk, c->st);
+        launch_reduce_cols(w.rpart, w.rblk, m, w.norms, c->st);
+        CK(cudaMemcpyAsync(w.h_norms, w.norms, m * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        for (int i = 0; i < m; ++i) {
+            bn2[i] = w.h_norms[i];
+            bn[i] = sqrt(bn2[i]);
+        }
+    }
+    if (hflag) return DSBCG_ERR_NONFINITE;
+
+    std::vector<double> rel((size_t)s * m, 0.0);
+    std::vector<int> conv((size_t)s * m, -1);
+    std::vector<int> conv_tmp((size_t)s * m, -1);
+    int total_steps = 0, restarts = 0, deflations = 0, final_rank = m;
+    long long mvms = 0;
+    dsbcg_status result = DSBCG_OK;
+    const bool mixed = prec != P64;
+    const double drop = mixed ? std::max(prm.restart_drop, 1e-12) : 0.0;
+
+    // --- joint inner solve on B for all shifts
+    {
+        std::vector<double> tg((size_t)s * m);
+        for (int j = 0; j < s; ++j)
+            for (int i = 0; i < m; ++i) tg[(size_t)j * m + i] = std::max(drop * bn[i], 0.5 * tol * bn[i]);
+        InnerResult ir;
+        CKS(inner_solve(c, w.B64, m, sigma, s, tg.data(), prec, dtol, prm.max_block_steps, prm.freeze_converged,
+                        prm.poll_every, &ir, 0, conv.data()));
+        total_steps += ir.steps;
+        mvms += ir.mvms;
+        deflations += ir.deflations;
+        final_rank = ir.final_rank;
+        if (ir.status == DSBCG_ERR_NOT_HPD) return DSBCG_ERR_NOT_HPD;
+        launch_accumulate(work_prec(prec), w.X64, ld, w.Xin, ld, s * m, n, c->st);
+    }
+    // --- FP64 true residuals
+    std::vector<double> r2(m);
+    for (int j = 0; j < s; ++j) {
+        CKS(true_residual(c, w.R64, w.B64, w.X64 + (size_t)j * m * ld, m, sigma[j], r2.data()));
+        mvms += m;
+        for (int i = 0; i < m; ++i) rel[(size_t)j * m + i] = bn[i] > 0 ? sqrt(r2[i]) / bn[i] : 0.0;
+    }
+    // --- per-shift restarts on the true residual
+    auto unconverged = [&](int j, std::vector<int>& cols) {
+        cols.clear();
+        for (int i = 0; i < m; ++i)
+            if (rel[(size_t)j * m + i] > tol) cols.push_back(i);
+    };
+    std::vector<int> cols;
+    bool any = false;
+    for (int j = 0; j < s; ++j) {
+        unconverged(j, cols);
+        if (!cols.empty()) any = true;
+    }
+    while (any && prm.refine && restarts < prm.max_restarts && total_steps < prm.max_block_steps) {
+        any = false;
+        for (int j = 0; j < s && restarts < prm.max_restarts; ++j) {
+            unconverged(j, cols);
+            if (cols.empty()) continue;
+            double2* Xj = w.X64 + (size_t)j * m * ld;
+            // recompute R_j (all columns) and gather the unconverged ones
+            CKS(true_residual(c, w.R64, w.B64, Xj, m, sigma[j], r2.data()));
+            mvms += m;
+            const int mu = (int)cols.size();
+            std::vector<double> tg(mu);
+            for (int q = 0; q < mu; ++q) {
+                int i = cols[q];
+                CK(cudaMemcpyAsync(w.rhs + (size_t)q * ld, w.R64 + (size_t)i * ld, db, cudaMemcpyDeviceToDevice, c->st));
+                double ri = sqrt(r2[i]);
+                tg[q] = std::max(drop * ri, 0.5 * tol * bn[i]);
+            }
+            InnerResult ir;
+            CKS(inner_solve(c, w.rhs, mu, &sigma[j], 1, tg.data(), prec, dtol,
+                            std::max(1, prm.max_block_steps - total_steps), prm.freeze_converged, prm.poll_every,
+                            &ir, total_steps, conv_tmp.data()));
+            total_steps += ir.steps;
+            mvms += ir.mvms;
+            deflations += ir.deflations;
+            restarts += 1;
+            if (ir.status == DSBCG_ERR_NOT_HPD) return DSBCG_ERR_NOT_HPD;
+            for (int q = 0; q < mu; ++q) {
+                launch_accumulate(work_prec(prec), Xj + (size_t)cols[q] * ld, ld,
+                                  (char*)w.Xin + (size_t)q * ld * prec_elem_bytes(work_prec(prec)), ld, 1, n, c->st);
+                if (conv_tmp[q] >= 0) conv[(size_t)j * m + cols[q]] = conv_tmp[q];
+            }
+            CKS(true_residual(c, w.R64, w.B64, Xj, m, sigma[j], r2.data()));
+            mvms += m;
+            for (int i = 0; i < m; ++i) rel[(size_t)j * m + i] = bn[i] > 0 ? sqrt(r2[i]) / bn[i] : 0.0;
+            unconverged(j, cols);
+            if (!cols.empty()) any = true;
+        }
+    }
+    for (double r : rel)
+        if (!(r <= tol)) result = DSBCG_NOT_CONVERGED;
+
+    // --- output X (canonical complex128 [s][m][n])
+    double2* xcanon = nullptr;
+    if (x_dev) {
+        xcanon = (double2*)X;
+        launch_unpack_fields(P64, xcanon, w.X64, ld, s * m, c->V, 1.f, c->st);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(c->st));
+    } else {
+        // stage one shift at a time through R64/T64a (m fields each)
+        for (int j = 0; j < s; ++j) {
+            launch_unpack_fields(P64, w.T64a, w.X64 + (size_t)j * m * ld, ld, m, c->V, 1.f, c->st);
+            CK(cudaMemcpyAsync((double2*)X + (size_t)j * m * n, w.T64a, (size_t)m * n * sizeof(double2),
+                               cudaMemcpyDeviceToHost, c->st));
+        }
+        CK(cudaStreamSynchronize(c->st));
+    }
+    prof_collect(c);
+    if (stats) {
+        stats->block_steps = total_steps;
+        stats->mvms = mvms;
+        stats->deflations = deflations;
+        stats->restarts = restarts;
+        stats->final_rank = final_rank;
+        if (stats->true_relres) memcpy(stats->true_relres, rel.data(), rel.size() * sizeof(double));
+        if (stats->conv_step) memcpy(stats->conv_step, conv.data(), conv.size() * sizeof(int));
+        for (int q = 0; q < 8; ++q) {
+            stats->kernel_ms[q] = c->kms[q];
+            stats->kernel_launches[q] = c->klaunch[q];
+        }
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return result;
+}
+
+dsbcg_status dsbcg_force(dsbcg_ctx* c, int m, int s, const void* X, const void* Lambda, const double* weights,
+                         int storage, void* dU) {
+    if (!c || !X || !Lambda || !dU || m < 1 || s < 1 || (size_t)m * s > 4096) return DSBCG_ERR_ARG;
+    if (storage != P64 && storage != P32) return DSBCG_ERR_UNSUPPORTED;
+    CKS(ensure_links(c, storage));
+    const size_t n = c->n, ld = c->ld, V = c->V;
+    const int nf = m * s;
+    const size_t fb = prec_elem_bytes(storage) * ld;
+    const size_t cb = (size_t)nf * n * sizeof(double2);
+    void *xf = nullptr, *lf = nullptr, *ex = nullptr, *el = nullptr;
+    double2 *stage = nullptr, *du = nullptr;
+    double* wf = nullptr;
+    dsbcg_status rs = DSBCG_OK;
+    if (cudaMalloc(&xf, nf * fb) || cudaMalloc(&lf, nf * fb) || cudaMalloc(&ex, nf * fb) ||
+        cudaMalloc(&el, nf * fb) || cudaMalloc((void**)&du, V * 36 * sizeof(double2)) ||
+        cudaMalloc((void**)&wf, nf * sizeof(double)))
+        rs = DSBCG_ERR_OOM;
+    const bool xd = is_device_ptr(X), ldv = is_device_ptr(Lambda), ud = is_device_ptr(dU);
+    if (rs == DSBCG_OK && (!xd || !ldv)) {
+        if (cudaMalloc((void**)&stage, cb)) rs = DSBCG_ERR_OOM;
+    }
+    if (rs == DSBCG_OK) {
+        std::vector<double> wh(nf);
+        for (int j = 0; j < s; ++j)
+            for (int i = 0; i < m; ++i) wh[(size_t)j * m + i] = weights ? weights[j] : 1.0;
+        cudaMemcpyAsync(wf, wh.data(), nf * sizeof(double), cudaMemcpyHostToDevice, c->st);
+        const double2* xs = (const double2*)X;
+        if (!xd) {
+            cudaMemcpyAsync(stage, X, cb, cudaMemcpyHostToDevice, c->st);
+            xs = stage;
+        }
+        launch_pack_fields(storage, xf, ld, xs, nf, V, 1.f, c->st);
+        const double2* ls = (const double2*)Lambda;
+        if (!ldv) {
+            cudaMemcpyAsync(stage, Lambda, cb, cudaMemcpyHostToDevice, c->st);
+            ls = stage;
+        }
+        launch_pack_fields(storage, lf, ld, ls, nf, V, 1.f, c->st);
+        launch_dslash(storage, ex, xf, ld, c->links[storage], c->g, c->kappa, 0, 0, nullptr, nf, std::min(nf, 16), 1.f,
+                      c->st);
+        launch_dslash(storage, el, lf, ld, c->links[storage], c->g, c->kappa, 0, 0, nullptr, nf, std::min(nf, 16), 1.f,
+                      c->st);
+        {
+            Prof p(c, DSBCG_KCLASS_OTHER);
+            launch_force(storage, du, ex, lf, el, xf, ld, nf, wf, c->g, c->kappa, c->st);
+        }
+        if (ud) {
+            cudaMemcpyAsync(dU, du, V * 36 * sizeof(double2), cudaMemcpyDeviceToDevice, c->st);
+        } else {
+            cudaMemcpyAsync(dU, du, V * 36 * sizeof(double2), cudaMemcpyDeviceToHost, c->st);
+        }
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->st) != cudaSuccess) rs = DSBCG_ERR_CUDA;
+        prof_collect(c);
+    }
+    cudaFree(xf);
+    cudaFree(lf);
+    cudaFree(ex);
+    cudaFree(el);
+    cudaFree(du);
+    cudaFree(wf);
+    if (stage) cudaFree(stage);
+    return rs;
+}
+
+}  // extern "C"

@@ -1,0 +1,282 @@
+"""Python binding of libdsbcg.so (C ABI in include/dsbcg.h).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA
+kernels.  PyTorch supplies device memory and streams.  There is no CPU
+fallback: if the compiled library is missing, every call raises.
+
+Entry points (same names as the C ABI):
+  Context(dims, U, kappa)           dsbcg_create / dsbcg_destroy
+  Context.solve(B, sigma, tol, ...) dsbcg_solve
+  Context.apply(op, fields, ...)    dsbcg_apply
+  Context.force(X, Lam, w, ...)     dsbcg_force
+  DSBCGSolve                        torch.autograd.Function around solve/force
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdsbcg.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "dsbcg.h")
+
+PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3}
+OPS = {"D": 0, "Ddag": 1, "A": 2}
+STATUS = {0: "OK", 1: "NOT_CONVERGED", -1: "ERR_ARG", -2: "ERR_NOT_HPD", -3: "ERR_CUDA",
+          -4: "ERR_OOM", -5: "ERR_NONFINITE", -6: "ERR_UNSUPPORTED"}
+KCLASS = ["dslash", "gram", "update", "shift", "small", "residual", "other", "unused"]
+
+
+class DSBCGError(RuntimeError):
+    def __init__(self, code, msg=""):
+        self.code = code
+        super().__init__(f"dsbcg status {code} ({STATUS.get(code, '?')}): {msg}")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("storage", ctypes.c_int), ("dtol", ctypes.c_double),
+                ("max_block_steps", ctypes.c_int), ("max_restarts", ctypes.c_int),
+                ("restart_drop", ctypes.c_double), ("poll_every", ctypes.c_int),
+                ("freeze_converged", ctypes.c_int), ("refine", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("block_steps", ctypes.c_int), ("mvms", ctypes.c_longlong),
+                ("deflations", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("final_rank", ctypes.c_int), ("seconds", ctypes.c_double),
+                ("true_relres", ctypes.POINTER(ctypes.c_double)),
+                ("conv_step", ctypes.POINTER(ctypes.c_int)),
+                ("kernel_ms", ctypes.c_double * 8), ("kernel_launches", ctypes.c_longlong * 8)]
+
+
+_lib_handle = None
+
+
+def lib():
+    """Load libdsbcg.so; raise if it has not been built."""
+    global _lib_handle
+    if _lib_handle is not None:
+        return _lib_handle
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1205_0359_gb300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.dsbcg_params_default.argtypes = [ctypes.POINTER(Params)]
+    L.dsbcg_params_default.restype = None
+    L.dsbcg_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int), vp, dp, ip, vp]
+    L.dsbcg_create.restype = ip
+    L.dsbcg_update_gauge.argtypes = [vp, vp]
+    L.dsbcg_update_gauge.restype = ip
+    L.dsbcg_solve.argtypes = [vp, ip, vp, ip, ctypes.POINTER(ctypes.c_double), dp,
+                              ctypes.POINTER(Params), vp, ctypes.POINTER(Stats)]
+    L.dsbcg_solve.restype = ip
+    L.dsbcg_apply.argtypes = [vp, ip, ip, ip, vp, vp]
+    L.dsbcg_apply.restype = ip
+    L.dsbcg_force.argtypes = [vp, ip, ip, vp, vp, ctypes.POINTER(ctypes.c_double), ip, vp]
+    L.dsbcg_force.restype = ip
+    L.dsbcg_set_profiling.argtypes = [vp, ip]
+    L.dsbcg_set_profiling.restype = ip
+    L.dsbcg_destroy.argtypes = [vp]
+    L.dsbcg_destroy.restype = None
+    L.dsbcg_error_string.argtypes = [ip]
+    L.dsbcg_error_string.restype = ctypes.c_char_p
+    L.dsbcg_version.argtypes = []
+    L.dsbcg_version.restype = ctypes.c_char_p
+    _lib_handle = L
+    return L
+
+
+def header_symbols(path: str = HEADER):
+    """Function names declared in include/dsbcg.h."""
+    txt = open(path).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(dsbcg_[a-z_0-9]+)\s*\(", txt)))
+
+
+def _check(code, what=""):
+    if code not in (0, 1):
+        raise DSBCGError(code, what + ": " + lib().dsbcg_error_string(code).decode())
+    return code
+
+
+def _ptr(t):
+    """Device or host address of a contiguous complex128 tensor or numpy array."""
+    if isinstance(t, torch.Tensor):
+        assert t.is_contiguous(), "tensor must be contiguous"
+        return ctypes.c_void_p(t.data_ptr())
+    assert isinstance(t, np.ndarray) and t.flags.c_contiguous
+    return ctypes.c_void_p(t.ctypes.data)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream) if torch.cuda.is_available() else None
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """One lattice, gauge field and kappa (dsbcg_create).
+
+    U: complex128 [Lt][Lz][Ly][Lx][4][3][3] (torch on CUDA or CPU, or numpy).
+    """
+
+    def __init__(self, dims, U, kappa, t_antiperiodic=True, stream=None):
+        self.dims = tuple(int(d) for d in dims)
+        self.kappa = float(kappa)
+        self.V = int(np.prod(self.dims))
+        self.n = 12 * self.V
+        self._ctx = ctypes.c_void_p()
+        self.stream = stream
+        d = (ctypes.c_int * 4)(*self.dims)
+        U = _as_c128(U)
+        _check(lib().dsbcg_create(ctypes.byref(self._ctx), d, _ptr(U), self.kappa,
+                                  int(bool(t_antiperiodic)), _stream_handle(stream)), "dsbcg_create")
+
+    def close(self):
+        if self._ctx:
+            lib().dsbcg_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def update_gauge(self, U):
+        _check(lib().dsbcg_update_gauge(self._ctx, _ptr(_as_c128(U))), "dsbcg_update_gauge")
+
+    def set_profiling(self, on=True):
+        _check(lib().dsbcg_set_profiling(self._ctx, int(bool(on))), "dsbcg_set_profiling")
+
+    def solve(self, B, sigma, tol, storage="fp32", out=None, dtol=0.0, max_block_steps=None,
+              max_restarts=None, restart_drop=None, poll_every=None, freeze=True, refine=True,
+              raise_on_error=True):
+        """X (s, m, n) complex128 for (sigma_j + A) X_j = B; B (m, n) complex128.
+
+        B and out may live on the GPU or on the host; the result has B's device.
+        Returns (X, stats dict)."""
+        B = _as_c128(B)
+        m = B.shape[0]
+        sig = np.ascontiguousarray(np.asarray(sigma, dtype=np.float64).reshape(-1))
+        s = sig.size
+        if out is None:
+            if isinstance(B, torch.Tensor):
+                out = torch.empty((s, m, self.n), dtype=torch.complex128, device=B.device)
+            else:
+                out = np.empty((s, m, self.n), dtype=np.complex128)
+        p = Params()
+        lib().dsbcg_params_default(ctypes.byref(p))
+        p.storage = PREC[storage] if isinstance(storage, str) else int(storage)
+        p.dtol = float(dtol)
+        if max_block_steps is not None:
+            p.max_block_steps = int(max_block_steps)
+        if max_restarts is not None:
+            p.max_restarts = int(max_restarts)
+        if restart_drop is not None:
+            p.restart_drop = float(restart_drop)
+        if poll_every is not None:
+            p.poll_every = int(poll_every)
+        p.freeze_converged = int(bool(freeze))
+        p.refine = int(bool(refine))
+        rel = np.zeros((s, m), dtype=np.float64)
+        conv = np.zeros((s, m), dtype=np.int32)
+        st = Stats()
+        st.true_relres = rel.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        st.conv_step = conv.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        code = lib().dsbcg_solve(self._ctx, m, _ptr(B), s,
+                                 sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(tol),
+                                 ctypes.byref(p), _ptr(out), ctypes.byref(st))
+        if raise_on_error:
+            _check(code, "dsbcg_solve")
+        stats = dict(status=STATUS.get(code, code), code=code, block_steps=st.block_steps,
+                     mvms=st.mvms, deflations=st.deflations, restarts=st.restarts,
+                     final_rank=st.final_rank, seconds=st.seconds, true_relres=rel,
+                     conv_step=conv,
+                     kernel_ms={KCLASS[q]: st.kernel_ms[q] for q in range(7)},
+                     kernel_launches={KCLASS[q]: st.kernel_launches[q] for q in range(7)})
+        return out, stats
+
+    def apply(self, op, fields, storage="fp64", out=None):
+        """op(fields) for op in {"D", "Ddag", "A"}; fields (m, n) complex128."""
+        fields = _as_c128(fields)
+        if out is None:
+            out = torch.empty_like(fields) if isinstance(fields, torch.Tensor) else np.empty_like(fields)
+        m = fields.shape[0]
+        _check(lib().dsbcg_apply(self._ctx, OPS[op], PREC[storage], m, _ptr(fields), _ptr(out)),
+               "dsbcg_apply")
+        return out
+
+    def force(self, X, Lam, weights=None, storage="fp64", out=None):
+        """Gauge-link gradient for solutions X and adjoint solutions Lam (s, m, n)."""
+        X = _as_c128(X)
+        Lam = _as_c128(Lam)
+        s, m, _ = X.shape
+        if out is None:
+            shape = self.dims[::-1] + (4, 3, 3)
+            if isinstance(X, torch.Tensor):
+                out = torch.empty(shape, dtype=torch.complex128, device=X.device)
+            else:
+                out = np.empty(shape, dtype=np.complex128)
+        w = None
+        if weights is not None:
+            w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64))
+            wp = w.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        else:
+            wp = None
+        _check(lib().dsbcg_force(self._ctx, m, s, _ptr(X), _ptr(Lam), wp, PREC[storage], _ptr(out)),
+               "dsbcg_force")
+        return out
+
+
+def _as_c128(t):
+    if isinstance(t, torch.Tensor):
+        if t.dtype != torch.complex128:
+            t = t.to(torch.complex128)
+        return t.contiguous()
+    return np.ascontiguousarray(np.asarray(t, dtype=np.complex128))
+
+
+class DSBCGSolve(torch.autograd.Function):
+    """X = DSBCGSolve.apply(B, sigma, U, ctx_args) with X_j = (sigma_j + A(U))^{-1} B.
+
+    B: (m, n) complex128 CUDA tensor; sigma: (s,) float64 tensor; U: gauge
+    field complex128 (Lt, Lz, Ly, Lx, 4, 3, 3).  ctx_args = dict(dims, kappa,
+    tol, storage).  The backward pass solves the adjoint systems
+    (sigma_j + A) Lambda_j = dL/dX_j (hermitian, so one more DSBlockCG call per
+    shift) and forms dL/dB = sum_j Lambda_j, dL/dsigma_j = -Re tr(Lambda_j^H X_j)
+    and dL/dU with the force kernel.
+    """
+
+    @staticmethod
+    def forward(ctx, B, sigma, U, args):
+        c = Context(args["dims"], U.detach(), args["kappa"])
+        X, stats = c.solve(B.detach(), sigma.detach().cpu().numpy(), args["tol"],
+                           storage=args.get("storage", "fp32"))
+        ctx.c = c
+        ctx.args = args
+        ctx.save_for_backward(X, sigma)
+        return X
+
+    @staticmethod
+    def backward(ctx, gX):
+        X, sigma = ctx.saved_tensors
+        c, args = ctx.c, ctx.args
+        sig = sigma.detach().cpu().numpy()
+        s = sig.size
+        gX = gX.contiguous()
+        Lam = torch.empty_like(X)
+        for j in range(s):
+            Lam[j:j + 1], _ = c.solve(gX[j], sig[j:j + 1], args.get("adj_tol", args["tol"]),
+                                      storage=args.get("storage", "fp32"))
+        gB = Lam.sum(dim=0)
+        gsig = -torch.real(torch.sum(torch.conj(Lam) * X, dim=(1, 2))).to(device=sigma.device, dtype=sigma.dtype)
+        gU = None
+        if ctx.needs_input_grad[2]:
+            gU = c.force(X, Lam, None, storage="fp64" if args.get("storage") == "fp64" else "fp32")
+        c.close()
+        return gB, gsig, gU, None

@@ -1,0 +1,158 @@
+"""GPU DSBlockCG parity against the FP64 oracle, through the C ABI.
+
+* 4^4 workload (b_4 = b_1 + b_2): FP64 and mixed precisions against dense LU
+  (relative error <= 1e-7 per (rhs, shift)), exact deflation, x_4 = x_1 + x_2;
+* fixed number of block steps: the GPU iterate equals the block Galerkin
+  iterate of Eq. 3.2 computed by the oracle's definition;
+* special cases m = s = 1 (CG), sigma = 0, a ragged lattice whose volume is
+  not a multiple of the CTA tiles, compared with the oracle's band-Lanczos
+  solver;
+* error paths: negative shift, NaN input, iteration cap;
+* the 16^3 x 32, m = s = 12 workload in the configuration bench.py times:
+  every true residual reported by the library <= tol, and sampled (i, j)
+  residuals recomputed with the oracle's own Wilson operator <= 10 tol.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import wilson as W
+from oracle.dsbcg import dense_solve, dsbcg as oracle_dsbcg, galerkin_iterate
+from paper_1205_0359_gb300 import dsbcg, synth
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda")
+
+
+@pytest.fixture(scope="module")
+def w1():
+    wl = synth.make_workload("w1_4x4x4x4")
+    Ad = W.dense_A(wl["U"], wl["kappa"], wl["dims"])
+    Xd = dense_solve(Ad, wl["B"], wl["sigma"])
+    ctx = dsbcg.Context(wl["dims"], torch.from_numpy(wl["U"]).to(DEV), wl["kappa"])
+    yield wl, Ad, Xd, ctx
+    ctx.close()
+
+
+def _relerr(X, Xd):
+    return np.linalg.norm(X - Xd, axis=-1) / np.linalg.norm(Xd, axis=-1)
+
+
+@pytest.mark.parametrize("storage,tol,bound", [("fp64", 1e-10, 1e-7), ("fp32", 1e-10, 1e-7),
+                                               ("fp16", 1e-10, 1e-7), ("bf16", 1e-8, 1e-5)])
+def test_w1_against_dense_lu(w1, storage, tol, bound):
+    wl, Ad, Xd, ctx = w1
+    B = torch.from_numpy(wl["B"]).to(DEV)
+    X, st = ctx.solve(B, wl["sigma"], tol, storage=storage)
+    Xg = X.cpu().numpy()
+    assert st["code"] == 0, st
+    assert st["true_relres"].max() <= tol
+    assert _relerr(Xg, Xd).max() <= bound
+    assert st["deflations"] >= 1
+    dep = np.linalg.norm(Xg[:, 3] - Xg[:, 0] - Xg[:, 1], axis=1) / np.linalg.norm(Xg[:, 3], axis=1)
+    assert dep.max() <= 10 * bound
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_fixed_k_galerkin_iterate(k):
+    dims = (2, 2, 2, 2)
+    rng = np.random.Generator(np.random.PCG64(31))
+    U = synth.su3_links(dims, 0.5, rng)
+    kappa = 0.12
+    n = 12 * synth.volume(dims)
+    B = synth.gaussian_rhs(n, 3, rng)
+    sigma = synth.log_shifts(1e-3, 1.0, 4)
+    Ad = W.dense_A(U, kappa, dims)
+    ctx = dsbcg.Context(dims, U, kappa)
+    X, st = ctx.solve(B, sigma, 0.0, storage="fp64", max_block_steps=k, refine=False, freeze=False,
+                      poll_every=1, raise_on_error=False)
+    assert st["code"] == 1 and st["block_steps"] == k
+    Xg = galerkin_iterate(Ad, B, sigma, k)
+    assert _relerr(X, Xg).max() < 1e-9
+    ctx.close()
+
+
+def test_fixed_k_with_deflation(w1):
+    wl, Ad, Xd, ctx = w1
+    X, st = ctx.solve(wl["B"], wl["sigma"], 0.0, storage="fp64", max_block_steps=2, refine=False,
+                      freeze=False, poll_every=1, raise_on_error=False)
+    assert st["deflations"] == 1 and st["final_rank"] == 3
+    Xg = galerkin_iterate(Ad, wl["B"], wl["sigma"], 2)
+    assert _relerr(X, Xg).max() < 1e-9
+
+
+def test_cg_special_case_and_zero_shift(w1):
+    wl, Ad, Xd, ctx = w1
+    b = wl["B"][:1]
+    for storage in ("fp64", "fp32"):
+        X, st = ctx.solve(b, [0.0], 1e-10, storage=storage)
+        want = dense_solve(Ad, b, [0.0])
+        assert st["code"] == 0 and _relerr(X, want).max() < 1e-7
+
+
+def test_ragged_lattice_against_oracle_solver():
+    dims = (6, 4, 4, 5)                         # 480 sites: 15 CTA tiles of 32
+    rng = np.random.Generator(np.random.PCG64(77))
+    U = synth.su3_links(dims, 0.5, rng)
+    kappa = 0.12
+    n = 12 * synth.volume(dims)
+    B = synth.gaussian_rhs(n, 5, rng)
+    sigma = synth.log_shifts(1e-2, 1.0, 3)
+    Aop = lambda v: W.A_vec(U, kappa, dims, v)
+    Xo, info = oracle_dsbcg(Aop, B, sigma, tol=1e-12)
+    assert info["converged"]
+    ctx = dsbcg.Context(dims, torch.from_numpy(U).to(DEV), kappa)
+    for storage in ("fp64", "fp32"):
+        X, st = ctx.solve(torch.from_numpy(B).to(DEV), sigma, 1e-11, storage=storage)
+        assert st["code"] == 0
+        assert _relerr(X.cpu().numpy(), Xo).max() < 1e-7
+    ctx.close()
+
+
+def test_error_paths(w1):
+    wl, Ad, Xd, ctx = w1
+    B = wl["B"]
+    with pytest.raises(dsbcg.DSBCGError) as e:
+        ctx.solve(B, [0.1, -1.0], 1e-8)
+    assert e.value.code == -1
+    Bn = B.copy()
+    Bn[1, 5] = np.nan
+    with pytest.raises(dsbcg.DSBCGError) as e:
+        ctx.solve(Bn, [0.1], 1e-8)
+    assert e.value.code == -5
+    X, st = ctx.solve(B, wl["sigma"], 1e-10, storage="fp64", max_block_steps=3, refine=False,
+                      raise_on_error=False)
+    assert st["code"] == 1 and st["status"] == "NOT_CONVERGED"
+    assert np.all(np.isfinite(X)) and st["true_relres"].max() > 1e-10
+    # the library still works after a capped solve
+    X, st = ctx.solve(B, wl["sigma"], 1e-10, storage="fp64")
+    assert st["code"] == 0
+
+
+def test_host_buffers_roundtrip(w1):
+    wl, Ad, Xd, ctx = w1
+    X, st = ctx.solve(wl["B"], wl["sigma"], 1e-10, storage="fp32")   # numpy in/out
+    assert isinstance(X, np.ndarray) and st["code"] == 0
+    assert _relerr(X, Xd).max() < 1e-7
+
+
+@pytest.fixture(scope="module")
+def w2():
+    wl = synth.make_workload("w2_16x16x16x32")
+    ctx = dsbcg.Context(wl["dims"], torch.from_numpy(wl["U"]).to(DEV), wl["kappa"])
+    yield wl, ctx
+    ctx.close()
+
+
+def test_w2_full_size_mixed(w2):
+    wl, ctx = w2
+    B = torch.from_numpy(wl["B"]).to(DEV)
+    X, st = ctx.solve(B, wl["sigma"], wl["tol"], storage="fp32")
+    assert st["code"] == 0, st
+    assert st["true_relres"].max() <= wl["tol"]
+    # independent check with the oracle's operator on sampled systems
+    for (j, i) in [(0, 0), (0, 11), (5, 3), (11, 7)]:
+        x = X[j, i].cpu().numpy()
+        r = wl["B"][i] - wl["sigma"][j] * x - W.A_vec(wl["U"], wl["kappa"], wl["dims"], x)
+        rel = np.linalg.norm(r) / np.linalg.norm(wl["B"][i])
+        assert rel <= 10 * wl["tol"], (j, i, rel)
