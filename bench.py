@@ -1,0 +1,362 @@
+#!/usr/bin/env python3
+"""Throughput of DSBlockCG on one GB300: (rhs x shift) systems solved per second.
+
+A step is one complete solve (sigma_j I + D^H D) X_j = B, j = 1..12, for
+12 right-hand sides on a 16^3 x 32 lattice (Wilson, kappa = 0.125, smooth
+random SU(3) links), to a true FP64 relative residual <= 1e-8 for every
+(rhs, shift): FP32 storage of fields and links, FP32 arithmetic on them,
+FP64 block coefficients, deflation, shift recurrences and true-residual
+restarts.  Inputs are resident in HBM when the timed region starts and the
+working set of one block step (~9 GB) is far larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (launched by torch.distributed.run)
+every rank solves its own replica; the value is all ranks' systems divided by
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "w2_16x16x16x32"
+METRIC = "(rhs×shift) systems/s at true residual 1e-8; D†D stencil GB/s vs HBM peak"
+UNIT = "systems/s"
+KCLASS = ["dslash", "gram", "update", "shift", "small", "residual", "other"]
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def workload_config(wl, storage):
+    return {
+        "workload": (f"{WORKLOAD}: Wilson D^H D on {'x'.join(map(str, wl['dims']))}, kappa {wl['kappa']}, "
+                     f"m={wl['B'].shape[0]} Z2 RHS, s={len(wl['sigma'])} shifts "
+                     f"{wl['sigma'][0]:.0e}..{wl['sigma'][-1]:.0e}, true residual <= {wl['tol']:.0e}, "
+                     f"{storage} storage + FP64 restarts"),
+        "lattice": list(wl["dims"]), "m": int(wl["B"].shape[0]), "s": int(len(wl["sigma"])),
+        "tol": wl["tol"], "storage": storage,
+        "l2": "no flush: one block step streams ~9 GB, far above the 129 MB L2",
+    }
+
+
+# ----------------------------------------------------------------- clocks --
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append(dict(sm=float(parts[1]), smax=float(parts[2]),
+                                     power=float(parts[3]) if parts[3] not in ("[N/A]", "") else 0.0,
+                                     hw=parts[5], hwt=parts[6], swt=parts[7], swp=parts[8]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("swp", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        loaded = [r["sm"] for r in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r["smax"] for r in rows),
+                "power_w_max": max(r["power"] for r in rows), "samples": len(rows),
+                "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------- traffic --
+def ncu_traffic(kclass):
+    """DRAM bytes / algorithmic bytes of a kernel class from the committed ncu
+    summary, or None when the summary is missing or the kernel source changed."""
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(path):
+        return None
+    src_hash = kernel_source_hash()
+    for line in open(path):
+        m = re.match(r"\|\s*" + kclass + r"\s*\|\s*([0-9.eE+]+)\s*\|\s*([0-9a-f]+)\s*\|", line)
+        if m and m.group(2) == src_hash:
+            return float(m.group(1))
+    return None
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1205_0359_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+# ------------------------------------------------------------ CPU oracle --
+def oracle_sample(wl, vectors, total_vectors):
+    """Time the FP64 oracle (numpy band-Lanczos DSBlockCG) on the same workload
+    for `vectors` Lanczos vectors and scale to a whole solve of
+    `total_vectors` vectors.  Returns (systems/s, cores used, seconds)."""
+    from oracle import wilson as W
+    from oracle.dsbcg import dsbcg as oracle_dsbcg
+    U, k, dims = wl["U"], wl["kappa"], wl["dims"]
+    Aop = lambda v: W.A_vec(U, k, dims, v)
+    c0, t0 = time.process_time(), time.perf_counter()
+    oracle_dsbcg(Aop, wl["B"], wl["sigma"], wl["tol"], freeze=False, stop_after_vectors=vectors)
+    wall = time.perf_counter() - t0
+    cpu = time.process_time() - c0
+    per_vec = wall / vectors
+    systems = wl["B"].shape[0] * len(wl["sigma"])
+    return systems / (per_vec * total_vectors), max(1, round(cpu / wall)), wall, per_vec
+
+
+# ------------------------------------------------------------- our arm --
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1205_0359_gb300 import dsbcg, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = synth.make_workload(WORKLOAD, dims=args.lattice)
+    m, s = wl["B"].shape[0], len(wl["sigma"])
+    n = wl["B"].shape[1]
+    stream = torch.cuda.current_stream(dev)
+    ctx = dsbcg.Context(wl["dims"], torch.from_numpy(wl["U"]).to(dev), wl["kappa"], stream=stream)
+    B = torch.from_numpy(wl["B"]).to(dev)
+    X = torch.empty((s, m, n), dtype=torch.complex128, device=dev)
+
+    def solve(storage=args.storage, Bx=B, Xx=X):
+        _, st = ctx.solve(Bx, wl["sigma"], wl["tol"], storage=storage, out=Xx)
+        return st
+
+    for _ in range(args.warmup):
+        solve()
+    ctx.set_profiling(True)
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats = [solve() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * m * s * args.steps / (ms_total / 1e3)
+    maxrel = max(float(st["true_relres"].max()) for st in stats)
+    ok = all(st["code"] == 0 for st in stats) and maxrel <= wl["tol"]
+
+    kms = {q: sum(st["kernel_ms"][q] for st in stats) for q in KCLASS}
+    kby = {q: sum(st["kernel_bytes"][q] for st in stats) for q in KCLASS}
+    kla = {q: sum(st["kernel_launches"][q] for st in stats) for q in KCLASS}
+    peak, peak_kind = load_peaks()
+    kernels = {}
+    for q in KCLASS:
+        if kms[q] > 0:
+            gbs = kby[q] / (kms[q] / 1e3) / 1e9
+            kernels[q] = {"ms_per_step": kms[q] / args.steps, "launches_per_step": kla[q] / args.steps,
+                          "GB_per_step": kby[q] / args.steps / 1e9, "GBps": gbs,
+                          "frac_of_hbm": gbs / peak}
+    memory_bound = [q for q in ("dslash", "gram", "update", "shift", "residual") if q in kernels]
+    dom = max(memory_bound, key=lambda q: kms[q])
+
+    def roof(q):
+        achieved = kby[q] / (kms[q] / 1e3) / 1e9
+        ratio = ncu_traffic(q)
+        per_launch = kby[q] / kla[q] if kla[q] else 0.0
+        return {"kernel": q, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": (None if ratio is None else round(ratio * per_launch / 1e9, 4)),
+                "traffic_unit": "GB per launch",
+                "algorithmic_GB_per_launch": round(kby[q] / kla[q] / 1e9, 4) if kla[q] else None,
+                "peak_source": f"{peak_kind} HBM copy bandwidth"}
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": workload_config(wl, args.storage),
+        "valid": ok, "max_true_relres": maxrel,
+        "solver": {"block_steps": stats[-1]["block_steps"], "restarts": stats[-1]["restarts"],
+                   "mvms": stats[-1]["mvms"], "deflations": stats[-1]["deflations"]},
+        "roofline": roof(dom),
+        "stencil_roofline": roof("dslash"),
+        "kernels": kernels,
+        "gpu_launches": int(sum(kla.values())),
+    }
+    if clk is not None:
+        line["clocks"] = clk
+    ctx.set_profiling(False)
+
+    # e2e: the same solve through the C ABI with pinned host buffers
+    Bh = torch.empty((m, n), dtype=torch.complex128, pin_memory=True)
+    Bh.copy_(torch.from_numpy(wl["B"]))
+    Xh = torch.empty((s, m, n), dtype=torch.complex128, pin_memory=True)
+    solve(Bx=Bh, Xx=Xh)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        solve(Bx=Bh, Xx=Xh)
+    torch.cuda.synchronize(dev)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    line["e2e"] = {"value": round(world * m * s / e2e_s, 3), "unit": UNIT,
+                   "h2d_bytes_per_step": int(Bh.numel() * 16), "d2h_bytes_per_step": int(Xh.numel() * 16)}
+
+    fp64_mvms = None
+    if rank == 0 and not args.no_fp64:
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st64 = solve(storage="fp64")
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        t64 = e0.elapsed_time(e1) / 1e3
+        fp64_mvms = st64["mvms"]
+        line["fp64_plain"] = {"value": round(m * s / t64, 4), "unit": UNIT, "ms_per_step": round(t64 * 1e3, 1),
+                              "block_steps": st64["block_steps"], "restarts": st64["restarts"],
+                              "max_true_relres": float(st64["true_relres"].max()),
+                              "mixed_over_fp64": round(value / world / (m * s / t64), 2)}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        total_vec = fp64_mvms if fp64_mvms else stats[-1]["mvms"]
+        v, cores, wall, per_vec = oracle_sample(wl, args.cpu_vectors, total_vec)
+        line["cpu_baseline"] = {
+            "value": round(v, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"numpy FP64 oracle, first {args.cpu_vectors} band-Lanczos vectors of the same "
+                       f"workload ({wall:.1f} s, {per_vec:.2f} s/vector), scaled to the "
+                       f"{total_vec} single-vector A applications of the FP64 GPU solve")}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------- reference arm --
+def run_reference(args):
+    """The FP64 CPU oracle on the host cores, as the reference implementation."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1205_0359_gb300 import synth
+    wl = synth.make_workload(WORKLOAD)
+    m, s = wl["B"].shape[0], len(wl["sigma"])
+    # whole-solve vector count of an FP64 DSBlockCG on this workload (block
+    # steps x m), as measured by the FP64 GPU form; used to scale each sample
+    total_vec = args.ref_total_vectors
+    for _ in range(args.warmup):
+        oracle_sample(wl, args.ref_vectors, total_vec)
+    vals, walls, cores = [], [], 1
+    for _ in range(args.steps):
+        v, cores, wall, _ = oracle_sample(wl, args.ref_vectors, total_vec)
+        vals.append(v)
+        walls.append(wall)
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * float(np.mean(walls)), 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(wl, "fp64"),
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": (f"each step: numpy FP64 oracle for {args.ref_vectors} band-Lanczos vectors, "
+                                    f"scaled to a {total_vec}-vector solve")},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16", "fp64"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--cpu-vectors", type=int, default=2)
+    ap.add_argument("--ref-vectors", type=int, default=1)
+    ap.add_argument("--ref-total-vectors", type=int, default=4200)
+    ap.add_argument("--lattice", type=lambda t: tuple(int(x) for x in t.split(",")), default=None,
+                    help="Lx,Ly,Lz,Lt to resize the workload (profiling of smaller cases)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -92,7 +92,10 @@ typedef struct {
                                (i, j) met its inner target (-1: never) */
     double kernel_ms[8];    /* if profiling is on: summed CUDA-event time per kernel
                                class (see DSBCG_KCLASS_*) */
-    long long kernel_launches[8];
+    long long kernel_launches[8];   /* kernels launched per class */
+    double kernel_bytes[8]; /* algorithmic HBM bytes per class: each operand field,
+                               link and coefficient block read or written once per
+                               launch, counted from the block widths of every step */
 } dsbcg_stats;
 
 /* kernel classes reported in dsbcg_stats.kernel_ms */

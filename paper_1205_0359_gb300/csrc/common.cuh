@@ -153,7 +153,14 @@ struct Ctl {
     int deflations;   // directions dropped so far
     long long mvms;   // single-vector A applications
     int last_step;    // last step that did work
-    int pad[6];
+    int pad[5];
+    // algorithmic traffic, in fields (one complex n-vector) moved to or from
+    // HBM, summed over block steps by the step's last kernel:
+    long long f_dslash;   // storage-precision fields read + written by the 2 stencils
+    long long f_gram;     // storage-precision fields read by the 2 Gram products
+    long long f_update;   // storage-precision fields of the block update
+    long long f_shift_s;  // storage-precision fields of the shift update (W in, V out)
+    long long f_shift_w;  // work-precision fields of the shift update (P_j, X_j)
 };
 
 // error codes mirrored from dsbcg.h

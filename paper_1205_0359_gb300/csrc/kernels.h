@@ -83,7 +83,7 @@ void launch_small_shift(SmallState* ss, Ctl* ctl, int s, int m, const double* si
                         const double* target_dev, int freeze, int wprec, void* coefU_w,
                         void* coefL_w, int* active, int* conv_step, double* res_out,
                         cudaStream_t st);
-void launch_small_finish(SmallState* ss, Ctl* ctl, int s, const int* active, cudaStream_t st);
+void launch_small_finish(SmallState* ss, Ctl* ctl, int s, int m, const int* active, cudaStream_t st);
 const double2* small_state_S(const SmallState* ss);
 
 // ---- force.cu ---------------------------------------------------------------

@@ -301,6 +301,7 @@ __global__ void small_init_kernel(SmallState* ss, Ctl* ctl, const double2* __res
         ctl->deflations = m - r;
         ctl->mvms = 0;
         ctl->last_step = 0;
+        ctl->f_dslash = ctl->f_gram = ctl->f_update = ctl->f_shift_s = ctl->f_shift_w = 0;
     }
 }
 
@@ -464,16 +465,24 @@ __global__ void small_shift_kernel(SmallState* ss, Ctl* ctl, int m, const double
     }
 }
 
-__global__ void small_finish_kernel(SmallState* ss, Ctl* ctl, int s) {
+__global__ void small_finish_kernel(SmallState* ss, Ctl* ctl, int s, int m, const int* __restrict__ active) {
     if (ctl->done) return;
-    int nalive = 0;
-    for (int j = 0; j < s; ++j) nalive += ss->sf[j].alive;
-    const int mk_ = ctl->mk, mn = ctl->mnext;
+    int nalive = 0, nkd = 0;
+    for (int j = 0; j < s; ++j) {
+        nalive += ss->sf[j].alive;
+        nkd += active[j];
+    }
+    const int mk_ = ctl->mk, mn = ctl->mnext, mp = ctl->k > 1 ? ctl->mprev : 0;
     // beta_k <- beta_{k+1}
     for (int t = threadIdx.x; t < M_MAX * M_MAX; t += blockDim.x) ss->sh.betak[t] = ss->sh.betan[t];
     __syncthreads();
     if (threadIdx.x == 0) {
         ctl->mvms += mk_;
+        ctl->f_dslash += 4LL * mk_;                 // D: V in, Z out; D^H: Z in, Y out
+        ctl->f_gram += 3LL * mk_;                   // V, Y for alpha; W for W^H W
+        ctl->f_update += 3LL * mk_ + mp;            // Y, V_k, V_{k-1} in, W out
+        ctl->f_shift_s += (long long)mk_ + mn;      // W in, V_{k+1} out
+        ctl->f_shift_w += (long long)nkd * (mk_ + mn + 2 * m);   // P_j in/out, X_j in/out
         ctl->last_step = ctl->k;
         ctl->nact = nalive;
         ctl->k += 1;
@@ -517,9 +526,8 @@ void launch_small_shift(SmallState* ss, Ctl* ctl, int s, int m, const double* si
                                           active, conv_step, res_out, MM);
 }
 
-void launch_small_finish(SmallState* ss, Ctl* ctl, int s, const int* active, cudaStream_t st) {
-    (void)active;
-    small_finish_kernel<<<1, 128, 0, st>>>(ss, ctl, s);
+void launch_small_finish(SmallState* ss, Ctl* ctl, int s, int m, const int* active, cudaStream_t st) {
+    small_finish_kernel<<<1, 128, 0, st>>>(ss, ctl, s, m, active);
 }
 
 }  // namespace dsbcg

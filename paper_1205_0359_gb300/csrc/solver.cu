@@ -59,6 +59,7 @@ struct dsbcg_ctx {
     std::vector<KEvent> ev_live;
     double kms[8] = {0};
     long long klaunch[8] = {0};
+    double kbytes[8] = {0};
     // workspace
     std::vector<void*> allocs;
     struct WS {
@@ -212,12 +213,12 @@ struct Prof {
     dsbcg_ctx* c;
     int cls;
     cudaEvent_t a = nullptr;
-    Prof(dsbcg_ctx* c_, int cls_) : c(c_), cls(cls_) {
+    Prof(dsbcg_ctx* c_, int cls_, int nlaunch = 1) : c(c_), cls(cls_) {
         if (c->profiling) {
             a = ev_get(c);
             cudaEventRecord(a, c->st);
         }
-        c->klaunch[cls] += 1;
+        c->klaunch[cls] += nlaunch;
     }
     ~Prof() {
         if (c->profiling) {
@@ -258,10 +259,13 @@ dsbcg_status true_residual(dsbcg_ctx* c, double2* r, const double2* b, const dou
     auto& w = c->ws;
     apply_A64(c, w.T64b, x, w.T64a, m);
     {
-        Prof p(c, DSBCG_KCLASS_RESIDUAL);
+        Prof p(c, DSBCG_KCLASS_RESIDUAL, 2);
         launch_residual(r, b, x, w.T64b, c->ld, m, c->n, sigma, w.rpart, w.rblk, c->st);
+        launch_reduce_cols(w.rpart, w.rblk, m, w.norms, c->st);
     }
-    launch_reduce_cols(w.rpart, w.rblk, m, w.norms, c->st);
+    // two FP64 stencils (m fields in and out, links once each) + b, x, Ax in, r out
+    c->kbytes[DSBCG_KCLASS_RESIDUAL] +=
+        (8.0 * m * c->n + 2.0 * 36 * c->V) * sizeof(double2);
     CK(cudaMemcpyAsync(w.h_norms, w.norms, m * sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     for (int i = 0; i < m; ++i) h_out[i] = w.h_norms[i];
@@ -297,14 +301,19 @@ dsbcg_status inner_solve(dsbcg_ctx* c, const double2* rhs, int m_in, const doubl
         Prof p(c, DSBCG_KCLASS_GRAM);
         launch_gram(P64, rhs, rhs, ld, n, nullptr, m_in, m_in, 1, 1, w.partials, w.nblk, 1.f, c->st);
     }
-    launch_gram_reduce(w.partials, w.nblk, m_in, 1, 1, w.G, w.diag, nullptr, m_in, c->st);
     {
-        Prof p(c, DSBCG_KCLASS_SMALL);
+        Prof p(c, DSBCG_KCLASS_SMALL, 2);
+        launch_gram_reduce(w.partials, w.nblk, m_in, 1, 1, w.G, w.diag, nullptr, m_in, c->st);
         launch_small_init(w.ss, w.ctl, w.G, w.diag, m_in, s_in, dtol, wp, w.coefS, c->st);
     }
     char* ring = (char*)w.vring;
-    launch_init_basis(prec, ring + 1 * (size_t)m_in * fb, ld, rhs, ld, n, small_state_S(w.ss), w.ctl, m_in,
-                      c->hscale, c->st);
+    {
+        Prof p(c, DSBCG_KCLASS_OTHER);
+        launch_init_basis(prec, ring + 1 * (size_t)m_in * fb, ld, rhs, ld, n, small_state_S(w.ss), w.ctl, m_in,
+                          c->hscale, c->st);
+    }
+    c->kbytes[DSBCG_KCLASS_GRAM] += (double)m_in * n * sizeof(double2);
+    c->kbytes[DSBCG_KCLASS_OTHER] += (double)m_in * n * (sizeof(double2) + prec_elem_bytes(prec));
     CK(cudaGetLastError());
     // block steps
     int step = 0;
@@ -329,7 +338,7 @@ dsbcg_status inner_solve(dsbcg_ctx* c, const double2* rhs, int m_in, const doubl
                 launch_gram(prec, Vk, w.y, ld, n, w.ctl, 0, m_in, 0, 1, w.partials, w.nblk, c->hscale, c->st);
             }
             {
-                Prof p(c, DSBCG_KCLASS_SMALL);
+                Prof p(c, DSBCG_KCLASS_SMALL, 2);
                 launch_gram_reduce(w.partials, w.nblk, m_in, 0, 1, w.alpha, w.yy, w.ctl, 0, c->st);
                 launch_small_alpha(w.ss, w.ctl, w.alpha, w.yy, wp, w.coef_a, w.coef_bh, c->st);
             }
@@ -343,7 +352,7 @@ dsbcg_status inner_solve(dsbcg_ctx* c, const double2* rhs, int m_in, const doubl
                 launch_gram(prec, w.zw, w.zw, ld, n, w.ctl, 0, m_in, 1, 0, w.partials, w.nblk, c->hscale, c->st);
             }
             {
-                Prof p(c, DSBCG_KCLASS_SMALL);
+                Prof p(c, DSBCG_KCLASS_SMALL, 3);
                 launch_gram_reduce(w.partials, w.nblk, m_in, 1, 0, w.G, w.diag, w.ctl, 0, c->st);
                 launch_small_qr(w.ss, w.ctl, w.G, dtol, wp, w.coefS, c->st);
                 launch_small_shift(w.ss, w.ctl, s_in, m_in, w.sigma, w.target, freeze, wp, w.coefU, w.coefL,
@@ -356,7 +365,7 @@ dsbcg_status inner_solve(dsbcg_ctx* c, const double2* rhs, int m_in, const doubl
             }
             {
                 Prof p(c, DSBCG_KCLASS_SMALL);
-                launch_small_finish(w.ss, w.ctl, s_in, w.active, c->st);
+                launch_small_finish(w.ss, w.ctl, s_in, m_in, w.active, c->st);
             }
         }
         CK(cudaGetLastError());
@@ -373,6 +382,14 @@ dsbcg_status inner_solve(dsbcg_ctx* c, const double2* rhs, int m_in, const doubl
             conv_step_host[t] = w.h_conv[t] >= 0 ? w.h_conv[t] + step_offset : -1;
     }
     const Ctl& h = *w.h_ctl;
+    {
+        const double eb = (double)prec_elem_bytes(prec) * n, wbn = (double)prec_elem_bytes(wp) * n;
+        const double links = 36.0 * c->V * (double)prec_elem_bytes(prec);
+        c->kbytes[DSBCG_KCLASS_DSLASH] += h.f_dslash * eb + 2.0 * h.last_step * links;
+        c->kbytes[DSBCG_KCLASS_GRAM] += h.f_gram * eb;
+        c->kbytes[DSBCG_KCLASS_UPDATE] += h.f_update * eb;
+        c->kbytes[DSBCG_KCLASS_SHIFT] += h.f_shift_s * eb + h.f_shift_w * wbn;
+    }
     out->steps = h.last_step;
     out->mvms = h.mvms;
     out->deflations = h.deflations;
@@ -576,6 +593,7 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
     for (int q = 0; q < 8; ++q) {
         c->kms[q] = 0;
         c->klaunch[q] = 0;
+        c->kbytes[q] = 0;
     }
 
     // --- inputs: B -> internal FP64 (staging through X64's storage if on the host)
@@ -588,16 +606,22 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
         CK(cudaMemcpyAsync(bcanon, B, (size_t)m * n * sizeof(double2), cudaMemcpyHostToDevice, c->st));
     }
     CK(cudaMemsetAsync(w.flag, 0, sizeof(int), c->st));
-    launch_check_finite(bcanon, (size_t)m * n, w.flag, c->st);
-    launch_pack_fields(P64, w.B64, ld, bcanon, m, c->V, 1.f, c->st);
+    {
+        Prof p(c, DSBCG_KCLASS_OTHER, 2);
+        launch_check_finite(bcanon, (size_t)m * n, w.flag, c->st);
+        launch_pack_fields(P64, w.B64, ld, bcanon, m, c->V, 1.f, c->st);
+    }
     int hflag = 0;
     CK(cudaMemcpyAsync(&hflag, w.flag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     CK(cudaMemsetAsync(w.X64, 0, (size_t)s * m * db, c->st));
     // ||b_i||^2 via the residual kernel with x = 0 (A 0 = 0)
     std::vector<double> bn2(m), bn(m);
     {
-        launch_residual(w.R64, w.B64, w.X64, w.X64, ld, m, n, 0.0, w.rpart, w.rblk, c->st);
-        launch_reduce_cols(w.rpart, w.rblk, m, w.norms, c->st);
+        {
+            Prof p(c, DSBCG_KCLASS_OTHER, 2);
+            launch_residual(w.R64, w.B64, w.X64, w.X64, ld, m, n, 0.0, w.rpart, w.rblk, c->st);
+            launch_reduce_cols(w.rpart, w.rblk, m, w.norms, c->st);
+        }
         CK(cudaMemcpyAsync(w.h_norms, w.norms, m * sizeof(double), cudaMemcpyDeviceToHost, c->st));
         CK(cudaStreamSynchronize(c->st));
         for (int i = 0; i < m; ++i) {
@@ -629,6 +653,7 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
         deflations += ir.deflations;
         final_rank = ir.final_rank;
         if (ir.status == DSBCG_ERR_NOT_HPD) return DSBCG_ERR_NOT_HPD;
+        Prof p(c, DSBCG_KCLASS_OTHER);
         launch_accumulate(work_prec(prec), w.X64, ld, w.Xin, ld, s * m, n, c->st);
     }
     // --- FP64 true residuals
@@ -677,6 +702,7 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
             restarts += 1;
             if (ir.status == DSBCG_ERR_NOT_HPD) return DSBCG_ERR_NOT_HPD;
             for (int q = 0; q < mu; ++q) {
+                Prof p(c, DSBCG_KCLASS_OTHER);
                 launch_accumulate(work_prec(prec), Xj + (size_t)cols[q] * ld, ld,
                                   (char*)w.Xin + (size_t)q * ld * prec_elem_bytes(work_prec(prec)), ld, 1, n, c->st);
                 if (conv_tmp[q] >= 0) conv[(size_t)j * m + cols[q]] = conv_tmp[q];
@@ -695,13 +721,19 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
     double2* xcanon = nullptr;
     if (x_dev) {
         xcanon = (double2*)X;
-        launch_unpack_fields(P64, xcanon, w.X64, ld, s * m, c->V, 1.f, c->st);
+        {
+            Prof p(c, DSBCG_KCLASS_OTHER);
+            launch_unpack_fields(P64, xcanon, w.X64, ld, s * m, c->V, 1.f, c->st);
+        }
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(c->st));
     } else {
         // stage one shift at a time through R64/T64a (m fields each)
         for (int j = 0; j < s; ++j) {
-            launch_unpack_fields(P64, w.T64a, w.X64 + (size_t)j * m * ld, ld, m, c->V, 1.f, c->st);
+            {
+                Prof p(c, DSBCG_KCLASS_OTHER);
+                launch_unpack_fields(P64, w.T64a, w.X64 + (size_t)j * m * ld, ld, m, c->V, 1.f, c->st);
+            }
             CK(cudaMemcpyAsync((double2*)X + (size_t)j * m * n, w.T64a, (size_t)m * n * sizeof(double2),
                                cudaMemcpyDeviceToHost, c->st));
         }
@@ -719,6 +751,7 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
         for (int q = 0; q < 8; ++q) {
             stats->kernel_ms[q] = c->kms[q];
             stats->kernel_launches[q] = c->klaunch[q];
+            stats->kernel_bytes[q] = c->kbytes[q];
         }
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }

@@ -50,7 +50,8 @@ class Stats(ctypes.Structure):
                 ("final_rank", ctypes.c_int), ("seconds", ctypes.c_double),
                 ("true_relres", ctypes.POINTER(ctypes.c_double)),
                 ("conv_step", ctypes.POINTER(ctypes.c_int)),
-                ("kernel_ms", ctypes.c_double * 8), ("kernel_launches", ctypes.c_longlong * 8)]
+                ("kernel_ms", ctypes.c_double * 8), ("kernel_launches", ctypes.c_longlong * 8),
+                ("kernel_bytes", ctypes.c_double * 8)]
 
 
 _lib_handle = None
@@ -198,7 +199,8 @@ class Context:
                      final_rank=st.final_rank, seconds=st.seconds, true_relres=rel,
                      conv_step=conv,
                      kernel_ms={KCLASS[q]: st.kernel_ms[q] for q in range(7)},
-                     kernel_launches={KCLASS[q]: st.kernel_launches[q] for q in range(7)})
+                     kernel_launches={KCLASS[q]: st.kernel_launches[q] for q in range(7)},
+                     kernel_bytes={KCLASS[q]: st.kernel_bytes[q] for q in range(7)})
         return out, stats
 
     def apply(self, op, fields, storage="fp64", out=None):
