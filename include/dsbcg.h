@@ -148,6 +148,36 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* ctx, int m, const void* B, int s, const doub
  *   in, out: device or host complex128 [m][n]; they may not overlap. */
 dsbcg_status dsbcg_apply(dsbcg_ctx* ctx, int op, int storage, int m, const void* in, void* out);
 
+/* Size of the library's static device scratch used by dsbcg_apply_static. */
+#define DSBCG_STATIC_SCRATCH_BYTES (32u << 20)
+
+/* dsbcg_apply without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc at the time
+ * of the call, e.g. code whose memory pool has already reserved the whole GPU,
+ * or latency-critical loops where cudaMalloc's implicit device
+ * synchronisation is not acceptable.  Same operation, arguments and result as
+ * dsbcg_apply, with these differences:
+ *   - in and out must be device pointers (host buffers would need staging);
+ *   - the packed working fields live in one static device array of
+ *     DSBCG_STATIC_SCRATCH_BYTES (32 MiB) that every GPU which loads the library
+ *     holds until the process exits.  op = A needs 3 * m * (n rounded up to a
+ *     multiple of 128) * (16, 8 or 4 bytes for FP64, FP32 or FP16/BF16) bytes,
+ *     D and D^H need 2/3 of that; larger requests return DSBCG_ERR_ARG and do
+ *     nothing;
+ *   - storage precisions other than FP64 need the context's links for that
+ *     precision to exist already (packed by an earlier dsbcg_apply or
+ *     dsbcg_solve with that precision); otherwise DSBCG_ERR_UNSUPPORTED, since
+ *     packing them would allocate;
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture;
+ *   - all calls share the array and it keeps the last call's contents; every
+ *     element a call reads is first written by the same call, so nothing needs
+ *     clearing, but calls that overlap on the GPU (different streams or
+ *     contexts in flight at once) race on it.
+ * The call synchronises the context's stream before returning. */
+dsbcg_status dsbcg_apply_static(dsbcg_ctx* ctx, int op, int storage, int m, const void* in, void* out);
+
 /* Gauge-link gradient ("fermion force") of a real loss through the solves
  * X_j = (sigma_j + A)^{-1} B, given adjoint solutions Lambda_j =
  * (sigma_j + A)^{-1} G_j of the incoming gradients G_j = dL/dX_j:

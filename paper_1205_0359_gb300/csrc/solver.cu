@@ -25,6 +25,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <mutex>
 #include <vector>
 
 #include "../../include/dsbcg.h"
@@ -823,3 +824,66 @@ dsbcg_status dsbcg_force(dsbcg_ctx* c, int m, int s, const void* X, const void* 
 }
 
 }  // extern "C"
+
+// ============================================================================
+// dsbcg_apply_static: dsbcg_apply with its working fields in a static device
+// array instead of cudaMalloc'd buffers (see include/dsbcg.h).
+static __device__ __align__(256) unsigned char g_apply_scratch[DSBCG_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+// Device address of g_apply_scratch on the current device, looked up once per
+// device (host code may not use the symbol itself as a device pointer).
+dsbcg_status static_scratch_address(void** out) {
+    static std::mutex mu;
+    static void* addr[128] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) {
+        cudaGetLastError();
+        return DSBCG_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_apply_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return DSBCG_ERR_CUDA;
+        }
+        addr[dev] = p;
+    }
+    *out = addr[dev];
+    return DSBCG_OK;
+}
+
+}  // namespace
+
+extern "C" dsbcg_status dsbcg_apply_static(dsbcg_ctx* c, int op, int storage, int m, const void* in, void* out) {
+    if (!c || !in || !out || m < 1 || op < 0 || op > 2 || storage < 0 || storage > 3) return DSBCG_ERR_ARG;
+    if (!is_device_ptr(in) || !is_device_ptr(out)) return DSBCG_ERR_ARG;
+    if (!c->links[storage]) return DSBCG_ERR_UNSUPPORTED;
+    const size_t ld = c->ld;
+    const size_t fb = prec_elem_bytes(storage) * ld;
+    const size_t nbuf = op == DSBCG_OP_A ? 3 : 2;
+    if ((size_t)m > (size_t)DSBCG_STATIC_SCRATCH_BYTES / (nbuf * fb)) return DSBCG_ERR_ARG;
+    void* base = nullptr;
+    CKS(static_scratch_address(&base));
+    char* a = (char*)base;
+    char* b = a + (size_t)m * fb;
+    char* t = b + (size_t)m * fb;
+    const double2* src = (const double2*)in;
+    double2* dst = (double2*)out;
+    launch_pack_fields(storage, a, ld, src, m, c->V, c->hscale, c->st);
+    if (op == DSBCG_OP_D) {
+        launch_dslash(storage, b, a, ld, c->links[storage], c->g, c->kappa, 0, 0, nullptr, m, m, c->hscale, c->st);
+    } else if (op == DSBCG_OP_DDAG) {
+        launch_dslash(storage, b, a, ld, c->links[storage], c->g, c->kappa, 1, 1, nullptr, m, m, c->hscale, c->st);
+    } else {
+        launch_dslash(storage, t, a, ld, c->links[storage], c->g, c->kappa, 0, 0, nullptr, m, m, c->hscale, c->st);
+        launch_dslash(storage, b, t, ld, c->links[storage], c->g, c->kappa, 1, 1, nullptr, m, m, c->hscale, c->st);
+    }
+    launch_unpack_fields(storage, dst, b, ld, m, c->V, c->hscale, c->st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->st));
+    return DSBCG_OK;
+}

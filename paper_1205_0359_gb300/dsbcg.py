@@ -77,6 +77,8 @@ def lib():
     L.dsbcg_solve.restype = ip
     L.dsbcg_apply.argtypes = [vp, ip, ip, ip, vp, vp]
     L.dsbcg_apply.restype = ip
+    L.dsbcg_apply_static.argtypes = [vp, ip, ip, ip, vp, vp]
+    L.dsbcg_apply_static.restype = ip
     L.dsbcg_force.argtypes = [vp, ip, ip, vp, vp, ctypes.POINTER(ctypes.c_double), ip, vp]
     L.dsbcg_force.restype = ip
     L.dsbcg_set_profiling.argtypes = [vp, ip]
@@ -211,6 +213,16 @@ class Context:
         m = fields.shape[0]
         _check(lib().dsbcg_apply(self._ctx, OPS[op], PREC[storage], m, _ptr(fields), _ptr(out)),
                "dsbcg_apply")
+        return out
+
+    def apply_static(self, op, fields, storage="fp64", out=None):
+        """dsbcg_apply_static: op(fields) with no device allocation in the
+        library; fields and out must be CUDA tensors (m, n) complex128."""
+        fields = _as_c128(fields)
+        if out is None:
+            out = torch.empty_like(fields)
+        _check(lib().dsbcg_apply_static(self._ctx, OPS[op], PREC[storage], fields.shape[0],
+                                        _ptr(fields), _ptr(out)), "dsbcg_apply_static")
         return out
 
     def force(self, X, Lam, weights=None, storage="fp64", out=None):
