@@ -11,7 +11,7 @@ size_t gram_partial_doubles(int nf_max) { return (size_t)ntiles_of(nf_max, 0) * 
 
 int gram_blocks(size_t n, int nf_max) {
     int tiles = ntiles_of(nf_max, 0);
-    int nb = (152 * 4 + tiles - 1) / tiles;
+    int nb = (152 * 8 + tiles - 1) / tiles;
     size_t maxb = (n + GT - 1) / GT;
     if ((size_t)nb > maxb) nb = (int)maxb;
     if (nb < 1) nb = 1;
@@ -42,7 +42,7 @@ void launch_gram_reduce(const double* partials, int nblk, int nf_max, int herm, 
     extern template void launch_ib_t<P>(void*, size_t, const double2*, size_t, size_t, const double2*,        \
                                         const Ctl*, int, float, cudaStream_t);                               \
     extern template void launch_su_t<P>(void*, const void*, const void*, size_t, void*, void*, size_t, size_t,  \
-                                        int, int, const Ctl*, int, const void*, const void*, const void*,     \
+                                        int, int, Ctl*, int, const void*, const void*, const void*,           \
                                         const int*, float, cudaStream_t);
 namespace blas_impl {
 EXTERN_P(P64)
@@ -74,7 +74,7 @@ void launch_init_basis(int prec, void* V1, size_t ldv, const double2* B, size_t 
 }
 
 void launch_shift_update(int prec, int wprec, void* Vnext, const void* W, const void* Vk, size_t ld, void* P,
-                         void* X, size_t ldw, size_t n, int s, int m, const Ctl* ctl, int nf_max,
+                         void* X, size_t ldw, size_t n, int s, int m, Ctl* ctl, int nf_max,
                          const void* coefS, const void* coefU, const void* coefL, const int* active,
                          float hscale, cudaStream_t st) {
     (void)wprec;

@@ -5,7 +5,8 @@
 //   shift_update  V_{k+1} = W S;  for every active shift j:
 //                 X_j += P_j Ut_j,  P_j <- V_{k+1} - P_j Lh_j
 //                 (the per-shift short recurrences of Sec. 3, all shifts in
-//                 one pass over HBM)
+//                 one pass over HBM), P_j and X_j streamed through shared
+//                 memory with bulk asynchronous copies.
 // Fields are flat complex n-vectors (internal order); each thread owns rows.
 // Accumulation is in the arithmetic precision of the storage (FP32 for
 // FP32/BF16/FP16 fields), reduced across threads in that precision and
@@ -60,7 +61,12 @@ __global__ void __launch_bounds__(GT) gram_kernel(const typename Tr<P>::S2* __re
     const int i0 = ti * 4, j0 = tj * 4;
     __shared__ R red[GT / 32][GSLOTS];
     if (i0 >= nf || j0 >= nf) {
-        if (threadIdx.x < GSLOTS) out[threadIdx.x] = 0.0;
+        if (threadIdx.x < GSLOTS) {
+            if constexpr (P == P64)
+                out[threadIdx.x] = 0.0;
+            else
+                reinterpret_cast<float*>(partials)[((size_t)tile * nblk + blockIdx.y) * GSLOTS + threadIdx.x] = 0.f;
+        }
         return;
     }
     const R inv = (P == PBF16 || P == PF16) ? R(1) / R(hscale) : R(1);
@@ -74,6 +80,7 @@ __global__ void __launch_bounds__(GT) gram_kernel(const typename Tr<P>::S2* __re
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = mk(R(0), R(0));
     }
+#pragma unroll 2
     for (size_t e = (size_t)blockIdx.y * GT + threadIdx.x; e < n; e += (size_t)nblk * GT) {
         C x[4], y[4];
 #pragma unroll
@@ -113,10 +120,20 @@ __global__ void __launch_bounds__(GT) gram_kernel(const typename Tr<P>::S2* __re
     }
     __syncthreads();
     if (threadIdx.x < GSLOTS) {
-        double sacc = 0.0;
+        if constexpr (P == P64) {
+            double sacc = 0.0;
 #pragma unroll
-        for (int ww = 0; ww < GT / 32; ++ww) sacc += (double)red[ww][threadIdx.x];
-        out[threadIdx.x] = sacc;
+            for (int ww = 0; ww < GT / 32; ++ww) sacc += red[ww][threadIdx.x];
+            out[threadIdx.x] = sacc;
+        } else {
+            // reduced precision: FP32 partials (FP64 arithmetic is slow on
+            // GB300 and the data carries FP32 accuracy), stored as floats in
+            // the same slot positions
+            float sacc = 0.f;
+#pragma unroll
+            for (int ww = 0; ww < GT / 32; ++ww) sacc += red[ww][threadIdx.x];
+            reinterpret_cast<float*>(partials)[((size_t)tile * nblk + blockIdx.y) * GSLOTS + threadIdx.x] = sacc;
+        }
     }
 }
 
@@ -177,16 +194,18 @@ __global__ void __launch_bounds__(256) block_update_kernel(typename Tr<P>::S2* _
     if (e >= n) return;
     const R inv = (P == PBF16 || P == PF16) ? R(1) / R(hscale) : R(1);
     const R scl = (P == PBF16 || P == PF16) ? R(hscale) : R(1);
-    C v[NF], vp[NF];
+    // every operand of the row is loaded before any arithmetic
+    C v[NF], vp[NF], y[NF];
 #pragma unroll
     for (int a = 0; a < NF; ++a) {
         v[a] = a < mk_ ? Elem<P>::ld(Vk + (size_t)a * ld, e, inv) : mk(R(0), R(0));
         vp[a] = a < mp ? Elem<P>::ld(Vp + (size_t)a * ld, e, inv) : mk(R(0), R(0));
+        y[a] = a < mk_ ? Elem<P>::ld(Y + (size_t)a * ld, e, inv) : mk(R(0), R(0));
     }
 #pragma unroll
     for (int b = 0; b < NF; ++b) {
         if (b < mk_) {
-            C w = Elem<P>::ld(Y + (size_t)b * ld, e, inv);
+            C w = y[b];
 #pragma unroll
             for (int a = 0; a < NF; ++a) {
                 cfms(w, v[a], sa[a * NF + b]);
@@ -226,34 +245,118 @@ __global__ void __launch_bounds__(256) init_basis_kernel(typename Tr<P>::S2* __r
 }
 
 // ---------------------------------------------------------------------------
-// Fused shift update.  One thread per row e.  For the first step of an inner
-// solve (k == 1) the search block of every shift is P_j = V_1 itself.
-template <int P, int PW, int NF>
-__global__ void __launch_bounds__(256) shift_update_kernel(
+// Fused shift update (the per-shift short recurrences of Sec. 3 for all
+// shifts in one pass over HBM):
+//     V_{k+1} = W S;  for every active shift j:
+//     X_j += P_j Ut_j,   P_j <- V_{k+1} - P_j Lh_j.
+// One thread per row e, ROWS rows per CTA.  The row tile of V_{k+1} stays in
+// shared memory across the shift loop.  The P_j and X_j tiles (one
+// contiguous ROWS-element run per field) are streamed with bulk asynchronous
+// copies (cp.async.bulk, completion on an mbarrier), double-buffered: while
+// shift j is computed, the tiles of the next active shift are in flight, and
+// the updated tiles of the previous one are written back with bulk stores.
+// Every mbarrier wait is bounded; on timeout the kernel records an error in
+// the control block, drains its own copies and returns.  For the first step
+// of an inner solve (k == 1) the search block is P_j = V_1 itself.
+constexpr int ST_WAIT_TIMEOUT = -3;        // reported to the host as DSBCG_ERR_CUDA
+constexpr long MBAR_SPIN_LIMIT = 1L << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// bounded wait; returns false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (long it = 0; it < MBAR_SPIN_LIMIT; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// rows per CTA: the double-buffered tiles take <= 80 KB of shared memory so
+// that 2-3 CTAs (and their compute phases) overlap on each SM
+template <int NF, int PW>
+__host__ __device__ constexpr int su_rows() {
+    return (NF * (int)sizeof(typename Tr<PW>::S2) * 128 * 5 <= 81920) ? 128 : 64;
+}
+template <int NF, int PW>
+__host__ __device__ constexpr size_t su_smem_bytes() {
+    return (size_t)5 * NF * su_rows<NF, PW>() * sizeof(typename Tr<PW>::S2)      // V tile + 2 x (P, X)
+           + (size_t)3 * NF * NF * sizeof(typename Tr<PW>::C) + 2 * sizeof(uint64_t) + 16;
+}
+
+template <int P, int PW, int NF, int ROWS>
+__global__ void __launch_bounds__(ROWS) shift_update_kernel(
     typename Tr<P>::S2* __restrict__ Vn, const typename Tr<P>::S2* __restrict__ W,
     const typename Tr<P>::S2* __restrict__ Vk, size_t ld, typename Tr<PW>::S2* __restrict__ Pb,
-    typename Tr<PW>::S2* __restrict__ Xb, size_t ldw, size_t n, int s, int m, const Ctl* __restrict__ ctl,
+    typename Tr<PW>::S2* __restrict__ Xb, size_t ldw, size_t n, int s, int m, Ctl* __restrict__ ctl,
     const typename Tr<PW>::C* __restrict__ cS, const typename Tr<PW>::C* __restrict__ cU,
     const typename Tr<PW>::C* __restrict__ cL, const int* __restrict__ active, float hscale) {
     using C = typename Tr<PW>::C;
     using R = typename Tr<PW>::R;
+    using E = typename Tr<PW>::S2;          // work-precision storage element (float2 / double2)
     if (ctl->done) return;
     const int mk_ = ctl->mk, mn = ctl->mnext, k = ctl->k;
-    __shared__ C sS[NF * NF], sU[NF * NF], sL[NF * NF];
-    for (int t = threadIdx.x; t < NF * NF; t += blockDim.x) sS[t] = cS[(t / NF) * M_MAX + (t % NF)];
-    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = e < n;
+    extern __shared__ __align__(128) unsigned char su_smem[];
+    E* sV = reinterpret_cast<E*>(su_smem);                    // [NF][ROWS]
+    E* sP[2] = {sV + NF * ROWS, sV + 3 * NF * ROWS};          // [NF][ROWS] each
+    E* sX[2] = {sV + 2 * NF * ROWS, sV + 4 * NF * ROWS};
+    C* sS = reinterpret_cast<C*>(sV + 5 * NF * ROWS);
+    C* sU = sS + NF * NF;
+    C* sL = sU + NF * NF;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sL + NF * NF);
+    const int tid = threadIdx.x;
+    const size_t e0 = (size_t)blockIdx.x * ROWS;
+    const int rows = (int)((n - e0) < (size_t)ROWS ? (n - e0) : (size_t)ROWS);
+    const uint32_t tile_bytes = (uint32_t)rows * sizeof(E);
+    const bool live = tid < rows;
+    const size_t e = e0 + tid;
     const float inv = (P == PBF16 || P == PF16) ? 1.f / hscale : 1.f;
     const float scl = (P == PBF16 || P == PF16) ? hscale : 1.f;
+
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    for (int t = tid; t < NF * NF; t += ROWS) sS[t] = cS[(t / NF) * M_MAX + (t % NF)];
     __syncthreads();
-    C v[NF];
+
+    // V_{k+1} = W S into the shared tile (and to HBM)
     if (live) {
         C w[NF];
 #pragma unroll
         for (int a = 0; a < NF; ++a) {
             if (a < mk_) {
-                auto t = Elem<P>::ld(W + (size_t)a * ld, e, inv);
-                w[a] = mk(R(t.x), R(t.y));
+                auto q = Elem<P>::ld(W + (size_t)a * ld, e, inv);
+                w[a] = mk(R(q.x), R(q.y));
             } else {
                 w[a] = mk(R(0), R(0));
             }
@@ -263,50 +366,105 @@ __global__ void __launch_bounds__(256) shift_update_kernel(
             C acc = mk(R(0), R(0));
 #pragma unroll
             for (int a = 0; a < NF; ++a) cfma(acc, w[a], sS[a * NF + c]);
-            v[c] = acc;
+            sV[c * ROWS + tid] = acc;
             if (c < mn) Elem<P>::st(Vn + (size_t)c * ld, e, mk((typename Tr<P>::R)acc.x, (typename Tr<P>::R)acc.y), scl);
         }
     }
-    for (int j = 0; j < s; ++j) {
-        if (!active[j]) continue;          // uniform across the grid
-        __syncthreads();
-        for (int t = threadIdx.x; t < NF * NF; t += blockDim.x) {
-            int a = t / NF, b = t % NF;
-            sU[t] = cU[((size_t)j * M_MAX + a) * M_MAX + b];
-            sL[t] = cL[((size_t)j * M_MAX + a) * M_MAX + b];
+
+    // tiles of shift j into buffer b (issued by thread 0)
+    auto issue = [&](int j, int b) {
+        const uint32_t np = (k > 1) ? (uint32_t)mk_ : 0u;
+        mbar_expect_tx(&bar[b], (np + (uint32_t)m) * tile_bytes);
+        const E* Pj = Pb + (size_t)j * m * ldw + e0;
+        const E* Xj = Xb + (size_t)j * m * ldw + e0;
+        for (uint32_t f = 0; f < np; ++f) bulk_g2s(sP[b] + f * ROWS, Pj + f * ldw, tile_bytes, &bar[b]);
+        for (int i = 0; i < m; ++i) bulk_g2s(sX[b] + i * ROWS, Xj + (size_t)i * ldw, tile_bytes, &bar[b]);
+    };
+
+    // every thread walks the same list of active shifts, so the pending and
+    // phase bookkeeping below is identical in all threads
+    int next = 0;
+    while (next < s && !active[next]) ++next;
+    uint32_t phase[2] = {0u, 0u};
+    bool pend[2] = {false, false};
+    if (next < s) {
+        if (tid == 0) issue(next, 0);
+        pend[0] = true;
+    }
+    bool ok = true;
+    for (int q = 0; next < s; ++q) {
+        const int j = next;
+        const int b = q & 1;
+        next = j + 1;
+        while (next < s && !active[next]) ++next;
+        if (next < s) {
+            if (tid == 0) {
+                bulk_wait_read_all();      // buffer b^1 may still be read by the previous shift's stores
+                issue(next, b ^ 1);
+            }
+            pend[b ^ 1] = true;
+        }
+        for (int t = tid; t < NF * NF; t += ROWS) {
+            sU[t] = cU[((size_t)j * M_MAX + t / NF) * M_MAX + t % NF];
+            sL[t] = cL[((size_t)j * M_MAX + t / NF) * M_MAX + t % NF];
+        }
+        if (mbar_wait(&bar[b], phase[b])) {
+            phase[b] ^= 1u;
+            pend[b] = false;
+        } else {
+            ok = false;
         }
         __syncthreads();
-        if (!live) continue;
-        typename Tr<PW>::S2* Pj = Pb + (size_t)j * m * ldw;     // m fields per shift
-        typename Tr<PW>::S2* Xj = Xb + (size_t)j * m * ldw;
-        C t[NF];
+        if (!__syncthreads_and(ok)) break;
+        if (live) {
+            C t[NF], x[NF];
 #pragma unroll
-        for (int a = 0; a < NF; ++a) {
-            if (a < mk_) {
-                if (k == 1) {
-                    auto q = Elem<P>::ld(Vk + (size_t)a * ld, e, inv);
-                    t[a] = mk(R(q.x), R(q.y));
+            for (int a = 0; a < NF; ++a) {
+                if (a < mk_) {
+                    if (k == 1) {
+                        auto v = Elem<P>::ld(Vk + (size_t)a * ld, e, inv);
+                        t[a] = mk(R(v.x), R(v.y));
+                    } else {
+                        t[a] = sP[b][a * ROWS + tid];
+                    }
                 } else {
-                    t[a] = Elem<PW>::ld(Pj + (size_t)a * ldw, e, R(1));
+                    t[a] = mk(R(0), R(0));
                 }
-            } else {
-                t[a] = mk(R(0), R(0));
+                x[a] = a < m ? sX[b][a * ROWS + tid] : mk(R(0), R(0));
+            }
+#pragma unroll
+            for (int i = 0; i < NF; ++i) {
+#pragma unroll
+                for (int a = 0; a < NF; ++a) cfma(x[i], t[a], sU[a * NF + i]);
+                if (i < m) sX[b][i * ROWS + tid] = x[i];
+            }
+#pragma unroll
+            for (int c = 0; c < NF; ++c) {
+                if (c < mn) {
+                    C p = sV[c * ROWS + tid];
+#pragma unroll
+                    for (int a = 0; a < NF; ++a) cfms(p, t[a], sL[a * NF + c]);
+                    sP[b][c * ROWS + tid] = p;
+                }
             }
         }
-        for (int i = 0; i < m; ++i) {
-            C x = Elem<PW>::ld(Xj + (size_t)i * ldw, e, R(1));
-#pragma unroll
-            for (int a = 0; a < NF; ++a) cfma(x, t[a], sU[a * NF + (i < NF ? i : 0)]);
-            Elem<PW>::st(Xj + (size_t)i * ldw, e, x, R(1));
+        fence_proxy_async();               // generic-proxy smem writes -> bulk stores
+        __syncthreads();
+        if (tid == 0) {
+            E* Pj = Pb + (size_t)j * m * ldw + e0;
+            E* Xj = Xb + (size_t)j * m * ldw + e0;
+            for (int c = 0; c < mn; ++c) bulk_s2g(Pj + (size_t)c * ldw, sP[b] + c * ROWS, tile_bytes);
+            for (int i = 0; i < m; ++i) bulk_s2g(Xj + (size_t)i * ldw, sX[b] + i * ROWS, tile_bytes);
+            bulk_commit();
         }
-#pragma unroll
-        for (int c = 0; c < NF; ++c) {
-            if (c < mn) {
-                C p = v[c];
-#pragma unroll
-                for (int a = 0; a < NF; ++a) cfms(p, t[a], sL[a * NF + c]);
-                Elem<PW>::st(Pj + (size_t)c * ldw, e, p, R(1));
-            }
+    }
+    if (tid == 0) {
+        bulk_wait_all();
+        if (!ok) {
+            // drain loads still in flight into either buffer (bounded), then report
+            for (int bb = 0; bb < 2; ++bb)
+                if (pend[bb]) mbar_wait(&bar[bb], phase[bb]);
+            atomicExch(&ctl->status, ST_WAIT_TIMEOUT);
         }
     }
 }
@@ -350,17 +508,27 @@ void launch_ib_t(void* V1, size_t ldv, const double2* B, size_t ldb, size_t n, c
 
 template <int P>
 void launch_su_t(void* Vnext, const void* W, const void* Vk, size_t ld, void* Pp, void* X, size_t ldw, size_t n,
-                 int s, int m, const Ctl* ctl, int nf_max, const void* coefS, const void* coefU, const void* coefL,
+                 int s, int m, Ctl* ctl, int nf_max, const void* coefS, const void* coefU, const void* coefL,
                  const int* active, float hscale, cudaStream_t st) {
     constexpr int PW = (P == P64) ? P64 : P32;
     using S2 = typename Tr<P>::S2;
     using W2 = typename Tr<PW>::S2;
     using CW = typename Tr<PW>::C;
-    int g = (int)((n + 255) / 256);
-#define BI_SU(NF)                                                                                        \
-    shift_update_kernel<P, PW, NF><<<g, 256, 0, st>>>((S2*)Vnext, (const S2*)W, (const S2*)Vk, ld, (W2*)Pp, (W2*)X, \
-                                                      ldw, n, s, m, ctl, (const CW*)coefS, (const CW*)coefU,        \
-                                                      (const CW*)coefL, active, hscale)
+#define BI_SU(NF)                                                                                           \
+    {                                                                                                       \
+        constexpr int ROWS = su_rows<NF, PW>();                                                             \
+        constexpr size_t SMEM = su_smem_bytes<NF, PW>();                                                    \
+        static bool attr = false;                                                                           \
+        if (!attr) {                                                                                        \
+            cudaFuncSetAttribute(shift_update_kernel<P, PW, NF, ROWS>,                                      \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);                    \
+            attr = true;                                                                                    \
+        }                                                                                                   \
+        int g = (int)((n + ROWS - 1) / ROWS);                                                               \
+        shift_update_kernel<P, PW, NF, ROWS><<<g, ROWS, SMEM, st>>>(                                        \
+            (S2*)Vnext, (const S2*)W, (const S2*)Vk, ld, (W2*)Pp, (W2*)X, ldw, n, s, m, ctl, (const CW*)coefS, \
+            (const CW*)coefU, (const CW*)coefL, active, hscale);                                            \
+    }
     BI_DISPATCH_NF(nf_max, BI_SU)
 #undef BI_SU
 }
@@ -371,7 +539,7 @@ void launch_su_t(void* Vnext, const void* W, const void* Vk, size_t ld, void* Pp
     template void launch_ib_t<P>(void*, size_t, const double2*, size_t, size_t, const double2*, const Ctl*, int, \
                                  float, cudaStream_t);                                                     \
     template void launch_su_t<P>(void*, const void*, const void*, size_t, void*, void*, size_t, size_t, int, int, \
-                                 const Ctl*, int, const void*, const void*, const void*, const int*, float,   \
+                                 Ctl*, int, const void*, const void*, const void*, const int*, float,         \
                                  cudaStream_t);
 
 }  // namespace blas_impl

@@ -3,14 +3,15 @@
 //   (D psi)(x) = psi(x) - kappa * sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu)
 //                                        + (1 + gamma_mu) U_mu(x-mu)^H psi(x-mu) ]
 //
-// One CTA covers 32 consecutive sites and every field of the block
-// (blockDim = 32 x nf_max).  The 8 links a site needs (4 forward, 4 backward)
-// are staged once per CTA in shared memory and applied to all fields, so each
-// link is read from global memory once per CTA and not once per field.
-// Each thread owns one (site, field) pair; a warp is 32 consecutive sites of
-// one field, so every pair-chunk load of a neighbour spinor is one contiguous
-// warp access (16 B per thread in FP32).
-//
+// One CTA of 32 threads covers 32 consecutive sites of one field; the grid
+// is (fields, site tiles) with the field index fastest, so the CTAs of all
+// fields of a site tile are issued together and the SU(3) links they share
+// are fetched from HBM once and then served from L1/L2 (read-only path).
+// Each thread owns one (site, field) pair; every pair-chunk load of a
+// neighbour spinor is one contiguous 512-byte warp access.  Staging the links
+// in shared memory per CTA was measured slower on GB300 (1.3 vs 3.3 TB/s at
+// 16^3 x 32 with 12 FP32 fields): the staging barrier serialises each CTA's
+// link and spinor loads.
 // Spin projection in the chiral basis (gamma_k = [[0, i s_k], [-i s_k, 0]],
 // gamma_4 = [[0, 1], [1, 0]]): with upper/lower spin pairs u = (p0, p1),
 // l = (p2, p3),
@@ -157,9 +158,11 @@ __device__ __forceinline__ int neighbour(const Geom& g, int x, const Site& s, in
     }
 }
 
-// Uh = U h (fwd) or U^H h (bwd) for the 2 x 3 half spinor h, link in smem
-template <class C>
-__device__ __forceinline__ void su3_mul(const C* __restrict__ u, int stride, const C h[2][3], C out[2][3], bool adj) {
+// Uh = U h (fwd) or U^H h (bwd) for the 2 x 3 half spinor h; entry e of the
+// link is at u[e * stride] (global memory, read-only path)
+template <int P, class C>
+__device__ __forceinline__ void su3_mul(const typename Tr<P>::S2* __restrict__ u, size_t stride, const C h[2][3],
+                                        C out[2][3], bool adj) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
 #pragma unroll
@@ -170,11 +173,11 @@ __device__ __forceinline__ void su3_mul(const C* __restrict__ u, int stride, con
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
             if (!adj) {
-                C uab = u[(a * 3 + b) * stride];
+                C uab = ld_link<P>(u + (a * 3 + b) * stride);
 #pragma unroll
                 for (int sp = 0; sp < 2; ++sp) cfma(out[sp][a], uab, h[sp][b]);
             } else {
-                C uba = u[(b * 3 + a) * stride];          // (U^H)_ab = conj(U_ba)
+                C uba = ld_link<P>(u + (b * 3 + a) * stride);     // (U^H)_ab = conj(U_ba)
 #pragma unroll
                 for (int sp = 0; sp < 2; ++sp) cfmac(out[sp][a], uba, h[sp][b]);
             }
@@ -183,47 +186,25 @@ __device__ __forceinline__ void su3_mul(const C* __restrict__ u, int stride, con
 }
 
 template <int P>
-__global__ void __launch_bounds__(512) dslash_kernel(typename Tr<P>::S2* __restrict__ out,
-                                                     const typename Tr<P>::S2* __restrict__ in,
-                                                     size_t ld, const typename Tr<P>::S2* __restrict__ links,
-                                                     Geom g, typename Tr<P>::R kappa, int g5in, int g5out,
-                                                     const Ctl* __restrict__ ctl, int nf_static, float hscale) {
+__global__ void __launch_bounds__(32) dslash_kernel(typename Tr<P>::S2* __restrict__ out,
+                                                   const typename Tr<P>::S2* __restrict__ in,
+                                                   size_t ld, const typename Tr<P>::S2* __restrict__ links,
+                                                   Geom g, typename Tr<P>::R kappa, int g5in, int g5out,
+                                                   const Ctl* __restrict__ ctl, int nf_static, float hscale,
+                                                   int nfg) {
     using C = typename Tr<P>::C;
     using R = typename Tr<P>::R;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* sl = reinterpret_cast<C*>(smem_raw);          // [8 dirs][9 entries][32 sites]
-
     int nf = nf_static;
     if (ctl) {
         if (ctl->done) return;
         nf = ctl->mk;
     }
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int site0 = blockIdx.x * 32;
+    // 1D grid: block b covers field b % nfg of site tile b / nfg (fields fastest)
+    const int f = (int)(blockIdx.x % (unsigned)nfg);
+    if (f >= nf) return;
+    const int tx = threadIdx.x;
+    const int site0 = (int)(blockIdx.x / (unsigned)nfg) * 32;
     const size_t V = (size_t)g.V;
-
-    // stage the 8 links of each of the 32 sites
-    const int nthr = blockDim.x * blockDim.y;
-    for (int idx = ty * 32 + tx; idx < 8 * 9 * 32; idx += nthr) {
-        int sx = idx & 31;
-        int e = (idx >> 5) % 9;
-        int d = idx / (9 * 32);
-        int x = site0 + sx;
-        C v = mk(R(0), R(0));
-        if (x < g.V) {
-            int mu = d & 3;
-            int src = x;
-            if (d >= 4) {
-                float sg;
-                Site s = coords(g, x);
-                src = neighbour(g, x, s, mu, -1, &sg);
-            }
-            v = ld_link<P>(links + ((size_t)mu * 9 + e) * V + src);
-        }
-        sl[(d * 9 + e) * 32 + sx] = v;
-    }
-    __syncthreads();
-
     const int x = site0 + tx;
     if (x >= g.V) return;
     const R inv = (P == PBF16 || P == PF16) ? R(1) / R(hscale) : R(1);
@@ -231,7 +212,7 @@ __global__ void __launch_bounds__(512) dslash_kernel(typename Tr<P>::S2* __restr
     const Site s = coords(g, x);
     const R g5i = g5in ? R(-1) : R(1);
 
-    for (int f = ty; f < nf; f += blockDim.y) {
+    {
         const typename Tr<P>::S2* fin = in + (size_t)f * ld;
         C acc[4][3];
 #pragma unroll
@@ -268,8 +249,8 @@ __global__ void __launch_bounds__(512) dslash_kernel(typename Tr<P>::S2* __restr
                     }
                 }
                 C uh[2][3];
-                const int d = dir == 0 ? mu : mu + 4;
-                su3_mul(sl + d * 9 * 32 + tx, 32, h, uh, dir != 0);
+                // forward hop: U_mu(x); backward hop: U_mu(x - mu) = U_mu(y)
+                su3_mul<P>(links + (size_t)mu * 9 * V + (dir == 0 ? x : y), V, h, uh, dir != 0);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     acc[0][a] = cadd(acc[0][a], uh[0][a]);
@@ -313,31 +294,33 @@ __global__ void __launch_bounds__(512) dslash_kernel(typename Tr<P>::S2* __restr
 void launch_dslash(int prec, void* out, const void* in, size_t ld, const void* links, const Geom& g,
                    double kappa, int g5in, int g5out, const Ctl* ctl, int nf_static, int nf_max,
                    float hscale, cudaStream_t st) {
-    int fy = nf_max < 16 ? nf_max : 16;
-    if (fy < 1) fy = 1;
-    dim3 block(32, fy);
-    dim3 grid((g.V + 31) / 32);
-    size_t sm = 8 * 9 * 32 * (prec == P64 ? sizeof(double2) : sizeof(float2));
+    // one CTA per (field, 32-site tile); with a control block the width is
+    // read on the device and bounded by nf_max, otherwise it is nf_static
+    const int nfg = ctl ? nf_max : nf_static;
+    const int nf_grid = nfg < 1 ? 1 : nfg;
+    dim3 block(32);
+    dim3 grid((unsigned)(nf_grid * ((g.V + 31) / 32)));
+    const size_t sm = 0;
     switch (prec) {
         case P64:
             dslash_kernel<P64><<<grid, block, sm, st>>>((double2*)out, (const double2*)in, ld,
                                                          (const double2*)links, g, kappa, g5in, g5out,
-                                                         ctl, nf_static, hscale);
+                                                         ctl, nf_static, hscale, nf_grid);
             break;
         case P32:
             dslash_kernel<P32><<<grid, block, sm, st>>>((float2*)out, (const float2*)in, ld,
                                                          (const float2*)links, g, (float)kappa, g5in,
-                                                         g5out, ctl, nf_static, hscale);
+                                                         g5out, ctl, nf_static, hscale, nf_grid);
             break;
         case PBF16:
             dslash_kernel<PBF16><<<grid, block, sm, st>>>((__nv_bfloat162*)out, (const __nv_bfloat162*)in, ld,
                                                            (const __nv_bfloat162*)links, g, (float)kappa,
-                                                           g5in, g5out, ctl, nf_static, hscale);
+                                                           g5in, g5out, ctl, nf_static, hscale, nf_grid);
             break;
         case PF16:
             dslash_kernel<PF16><<<grid, block, sm, st>>>((__half2*)out, (const __half2*)in, ld,
                                                           (const __half2*)links, g, (float)kappa, g5in,
-                                                          g5out, ctl, nf_static, hscale);
+                                                          g5out, ctl, nf_static, hscale, nf_grid);
             break;
     }
 }

@@ -64,25 +64,26 @@ void launch_block_update(int prec, void* W, const void* Y, const void* Vk, const
 void launch_init_basis(int prec, void* V1, size_t ldv, const double2* B, size_t ldb, size_t n,
                        const double2* S, const Ctl* ctl, int nf_in, float hscale, cudaStream_t st);
 // fused shift update (kernel (d)): V_{k+1} = W S; for active shifts
-// X_j += P_j Ut_j and P_j <- V_{k+1} - P_j LhT_j
+// X_j += P_j Ut_j and P_j <- V_{k+1} - P_j LhT_j.  P and X hold s blocks of
+// m fields of ldw elements (field-major, like every other block).
 void launch_shift_update(int prec, int wprec, void* Vnext, const void* W, const void* Vk,
                          size_t ld, void* P, void* X, size_t ldw, size_t n, int s, int m,
-                         const Ctl* ctl, int nf_max, const void* coefS, const void* coefU,
+                         Ctl* ctl, int nf_max, const void* coefS, const void* coefU,
                          const void* coefL, const int* active, float hscale, cudaStream_t st);
 
 // ---- small.cu ---------------------------------------------------------------
 struct SmallState;     // device FP64 m x m state, defined in small.cu
 size_t small_state_bytes(int s);
 void launch_small_init(SmallState* ss, Ctl* ctl, const double2* G0, const double* ref, int m,
-                       int s, double dtol, int wprec, void* coefS_w, cudaStream_t st);
-void launch_small_alpha(SmallState* ss, const Ctl* ctl, const double2* alpha, const double* yy,
+                       int s, double dtol, cudaStream_t st);
+// alpha_k from the Gram partials of V_k^H Y (+ coefficient tiles for the block update)
+void launch_small_alpha(SmallState* ss, const Ctl* ctl, const double* partials, int nblk, int nf_max,
                         int wprec, void* coef_a, void* coef_bh, cudaStream_t st);
-void launch_small_qr(SmallState* ss, Ctl* ctl, const double2* G, double dtol, int wprec,
-                     void* coefS_w, cudaStream_t st);
-void launch_small_shift(SmallState* ss, Ctl* ctl, int s, int m, const double* sigma_dev,
-                        const double* target_dev, int freeze, int wprec, void* coefU_w,
-                        void* coefL_w, int* active, int* conv_step, double* res_out,
-                        cudaStream_t st);
+// W^H W from the Gram partials, pivoted QR with deflation, per-shift recurrences
+void launch_small_step(SmallState* ss, Ctl* ctl, const double* partials, int nblk, int s, int m,
+                       double dtol, const double* sigma_dev, const double* target_dev, int freeze,
+                       int wprec, void* coefS_w, void* coefU_w, void* coefL_w, int* active,
+                       int* conv_step, double* res_out, cudaStream_t st);
 void launch_small_finish(SmallState* ss, Ctl* ctl, int s, int m, const int* active, cudaStream_t st);
 const double2* small_state_S(const SmallState* ss);
 

@@ -57,21 +57,35 @@ const double2* small_state_S(const SmallState* ss) { return ss->sh.S; }
 
 namespace {
 
-constexpr int NT = 128;
+// All m x m arithmetic runs on the first warp of a CTA and synchronises with
+// __syncwarp: the matrices are at most 32 x 32, so one warp has enough
+// parallelism and block-wide barriers would dominate the run time.
+constexpr int WS = 32;
+constexpr int NT = 128;            // threads of the CTAs that also reduce partial sums
+constexpr int GSL = 36;            // slots per 4 x 4 tile in the Gram partials
 
 __device__ __forceinline__ double2 z2() { return make_double2(0.0, 0.0); }
 __device__ __forceinline__ double2 conjd(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cmuld(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ void wsync() { __syncwarp(); }
 
-// dst (r x c, leading dim ld) <- src (M_MAX layout), zero outside
+// Block-wide helpers (all threads of the CTA, __syncthreads): GB300 issues
+// FP64 at a small fraction of the FP32 rate per SM sub-partition, so the
+// m x m products are spread over all four of them.
+__device__ __forceinline__ void bsync() { __syncthreads(); }
+
+// dst (r x c valid, R x Cc written, leading dim ld) <- src (M_MAX layout)
 __device__ void ld_mat(double2* dst, int ld, const double2* src, int r, int c, int R, int Cc) {
     for (int t = threadIdx.x; t < R * Cc; t += blockDim.x) {
         int i = t / Cc, j = t % Cc;
         dst[i * ld + j] = (i < r && j < c) ? src[i * M_MAX + j] : z2();
     }
 }
+// full M_MAX x M_MAX tile in the work precision, zero outside r x c
 template <class C>
 __device__ void st_mat_w(C* dst, const double2* src, int ld, int r, int c) {
-    // full M_MAX x M_MAX tile, zero outside r x c
     for (int t = threadIdx.x; t < M_MAX * M_MAX; t += blockDim.x) {
         int i = t / M_MAX, j = t % M_MAX;
         double2 v = (i < r && j < c) ? src[i * ld + j] : z2();
@@ -85,73 +99,7 @@ __device__ void st_mat_work(int wprec, void* dst, const double2* src, int ld, in
         st_mat_w((float2*)dst, src, ld, r, c);
 }
 
-// In-place Cholesky A = L L^H (n x n, lower part), returns 0 on failure
-__device__ int chol(double2* A, int ld, int n) {
-    __shared__ int ok;
-    if (threadIdx.x == 0) ok = 1;
-    __syncthreads();
-    for (int p = 0; p < n; ++p) {
-        if (threadIdx.x == 0) {
-            double d = A[p * ld + p].x;
-            if (!(d > 0.0)) {
-                ok = 0;
-                d = 1.0;
-            }
-            A[p * ld + p] = make_double2(sqrt(d), 0.0);
-        }
-        __syncthreads();
-        double lpp = A[p * ld + p].x;
-        for (int i = p + 1 + threadIdx.x; i < n; i += blockDim.x) {
-            A[i * ld + p] = make_double2(A[i * ld + p].x / lpp, A[i * ld + p].y / lpp);
-        }
-        __syncthreads();
-        // trailing update A_ij -= L_ip conj(L_jp), i >= j > p
-        int rem = n - p - 1;
-        for (int t = threadIdx.x; t < rem * rem; t += blockDim.x) {
-            int i = p + 1 + t / rem, j = p + 1 + t % rem;
-            if (j <= i) {
-                double2 a = A[i * ld + p], b = A[j * ld + p];
-                double2 v = A[i * ld + j];
-                v.x -= a.x * b.x + a.y * b.y;
-                v.y -= a.y * b.x - a.x * b.y;
-                A[i * ld + j] = v;
-            }
-        }
-        __syncthreads();
-    }
-    return ok;
-}
-
-// Solve (L L^H) X = B in place for nrhs columns of B (n x nrhs, ld ldb)
-__device__ void chol_solve(const double2* L, int ld, int n, double2* B, int ldb, int nrhs) {
-    for (int c = threadIdx.x; c < nrhs; c += blockDim.x) {
-        // forward: L y = b
-        for (int i = 0; i < n; ++i) {
-            double2 s = B[i * ldb + c];
-            for (int q = 0; q < i; ++q) {
-                double2 l = L[i * ld + q], y = B[q * ldb + c];
-                s.x -= l.x * y.x - l.y * y.y;
-                s.y -= l.x * y.y + l.y * y.x;
-            }
-            double d = L[i * ld + i].x;
-            B[i * ldb + c] = make_double2(s.x / d, s.y / d);
-        }
-        // backward: L^H x = y
-        for (int i = n - 1; i >= 0; --i) {
-            double2 s = B[i * ldb + c];
-            for (int q = i + 1; q < n; ++q) {
-                double2 l = conjd(L[q * ld + i]), x = B[q * ldb + c];
-                s.x -= l.x * x.x - l.y * x.y;
-                s.y -= l.x * x.y + l.y * x.x;
-            }
-            double d = L[i * ld + i].x;
-            B[i * ldb + c] = make_double2(s.x / d, s.y / d);
-        }
-    }
-    __syncthreads();
-}
-
-// C (r x c) = op(A) (r x q) * op(B) (q x c); ta/tb: 0 = plain, 1 = conj transpose
+// C (r x c) = alpha op(A) op(B) + beta C; op: 0 plain, 1 conjugate transpose
 __device__ void gemm(double2* Cm, int ldc, const double2* A, int lda, int ta, const double2* B, int ldb, int tb,
                      int r, int q, int c, double alpha, double beta) {
     for (int t = threadIdx.x; t < r * c; t += blockDim.x) {
@@ -166,63 +114,99 @@ __device__ void gemm(double2* Cm, int ldc, const double2* A, int lda, int ta, co
         double2 o = beta != 0.0 ? Cm[i * ldc + j] : z2();
         Cm[i * ldc + j] = make_double2(beta * o.x + alpha * s.x, beta * o.y + alpha * s.y);
     }
-    __syncthreads();
+    bsync();
+}
+
+// In-place inverse of a hermitian positive definite n x n matrix by
+// Gauss-Jordan elimination without pivoting (its pivots are the Schur
+// complement diagonals, positive for hpd).  Returns 0 if a pivot is <= 0.
+__device__ int gj_inverse(double2* A, int ld, int n, double2* col) {
+    int ok = 1;
+    for (int p = 0; p < n; ++p) {
+        double d = A[p * ld + p].x;
+        if (!(d > 0.0)) {
+            ok = 0;
+            d = 1.0;
+        }
+        const double inv = 1.0 / d;
+        for (int r = threadIdx.x; r < n; r += blockDim.x) col[r] = A[r * ld + p];
+        bsync();
+        for (int c = threadIdx.x; c < n; c += blockDim.x) {
+            double2 v = A[p * ld + c];
+            A[p * ld + c] = (c == p) ? make_double2(inv, 0.0) : make_double2(v.x * inv, v.y * inv);
+        }
+        bsync();
+        for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+            int r = t / n, c = t % n;
+            if (r == p) continue;
+            double2 f = col[r];
+            if (c == p) {
+                A[r * ld + p] = make_double2(-f.x * inv, -f.y * inv);
+            } else {
+                double2 a = A[p * ld + c], v = A[r * ld + c];
+                v.x -= f.x * a.x - f.y * a.y;
+                v.y -= f.x * a.y + f.y * a.x;
+                A[r * ld + c] = v;
+            }
+        }
+        bsync();
+    }
+    return ok;
 }
 
 // Pivoted Cholesky of the hermitian Gram matrix G (n x n, smem, ld) with the
-// deflation test d_q <= dtol^2 ref_q.  Produces rank r, the permutation, the
-// r x n factor R (permuted column order), S = Pi_r R11^{-1} (n x r) and
-// beta = R Pi^T (r x n) written to global (M_MAX layout).
-__device__ int pivoted_qr(double2* G, int ld, int n, const double* ref, double dtol, double2* Rm,
-                          double2* Sg, double2* betag, int* perm_s, double* dd) {
-    __shared__ int rank_s, piv_s;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        perm_s[i] = i;
+// deflation test: remaining squared norm <= dtol^2 * ref (the column's
+// squared norm when it was created).  Pivot: the largest remaining relative
+// squared norm, ties to the lowest index.  Produces the rank r, the r x n
+// factor R in permuted column order (Rm, ld n), S = Pi_r R11^{-1} (n x r)
+// and beta = R Pi^T (r x n), both in smem with leading dimension ld.
+__device__ int pivoted_qr(const double2* G, int ld, int n, const double* ref, double dtol, double2* Rm,
+                          double2* S, double2* beta, int* perm, double* dd) {
+    for (int i = threadIdx.x; i < n; i += WS) {
+        perm[i] = i;
         dd[i] = G[i * ld + i].x;
     }
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) Rm[t] = z2();
-    if (threadIdx.x == 0) rank_s = n;
-    __syncthreads();
+    for (int t = threadIdx.x; t < n * n; t += WS) Rm[t] = z2();
+    wsync();
+    int rank = n;
     for (int p = 0; p < n; ++p) {
-        if (threadIdx.x == 0) {
-            // largest remaining relative squared norm, ties to the lowest index
-            int best = -1;
-            double bv = -1.0;
-            for (int q = p; q < n; ++q) {
-                double r = ref[perm_s[q]];
-                double v = (r > 0.0) ? dd[q] / r : -1.0;
-                if (v > bv) {
-                    bv = v;
-                    best = q;
-                }
-            }
-            if (best < 0 || !(bv > dtol * dtol) || !(dd[best] > 0.0)) {
-                rank_s = p;
-                piv_s = -1;
-            } else {
-                piv_s = best;
-                if (best != p) {
-                    int tp = perm_s[p];
-                    perm_s[p] = perm_s[best];
-                    perm_s[best] = tp;
-                    double td = dd[p];
-                    dd[p] = dd[best];
-                    dd[best] = td;
-                    for (int l = 0; l < p; ++l) {
-                        double2 tr = Rm[l * n + p];
-                        Rm[l * n + p] = Rm[l * n + best];
-                        Rm[l * n + best] = tr;
-                    }
-                }
-                Rm[p * n + p] = make_double2(sqrt(dd[p]), 0.0);
+        // pivot choice: every lane scans the same (short) candidate list
+        int best = -1;
+        double bv = -1.0;
+        for (int q = p; q < n; ++q) {
+            double r = ref[perm[q]];
+            double v = (r > 0.0) ? dd[q] / r : -1.0;
+            if (v > bv) {
+                bv = v;
+                best = q;
             }
         }
-        __syncthreads();
-        if (piv_s < 0) break;
-        const double rpp = Rm[p * n + p].x;
-        const int gp = perm_s[p];
-        for (int r = p + 1 + threadIdx.x; r < n; r += blockDim.x) {
-            const int gr = perm_s[r];
+        wsync();
+        if (best < 0 || !(bv > dtol * dtol) || !(dd[best] > 0.0)) {
+            rank = p;
+            break;
+        }
+        if (best != p) {
+            if (threadIdx.x == 0) {
+                int tp = perm[p];
+                perm[p] = perm[best];
+                perm[best] = tp;
+                double td = dd[p];
+                dd[p] = dd[best];
+                dd[best] = td;
+            }
+            for (int l = threadIdx.x; l < p; l += WS) {
+                double2 tr = Rm[l * n + p];
+                Rm[l * n + p] = Rm[l * n + best];
+                Rm[l * n + best] = tr;
+            }
+            wsync();
+        }
+        const double rpp = sqrt(dd[p]);
+        const int gp = perm[p];
+        if (threadIdx.x == 0) Rm[p * n + p] = make_double2(rpp, 0.0);
+        for (int r = p + 1 + threadIdx.x; r < n; r += WS) {
+            const int gr = perm[r];
             double2 s = G[gp * ld + gr];
             for (int l = 0; l < p; ++l) {
                 double2 a = conjd(Rm[l * n + p]), b = Rm[l * n + r];
@@ -233,63 +217,124 @@ __device__ int pivoted_qr(double2* G, int ld, int n, const double* ref, double d
             Rm[p * n + r] = s;
             dd[r] -= s.x * s.x + s.y * s.y;
         }
-        __syncthreads();
+        wsync();
     }
-    const int r = rank_s;
     // beta = R Pi^T : beta[c'][perm[c]] = R[c'][c]
-    for (int t = threadIdx.x; t < M_MAX * M_MAX; t += blockDim.x) betag[t] = z2();
-    __syncthreads();
-    for (int t = threadIdx.x; t < r * n; t += blockDim.x) {
+    for (int t = threadIdx.x; t < n * n; t += WS) {
         int cp = t / n, c = t % n;
-        betag[cp * M_MAX + perm_s[c]] = (c >= cp) ? Rm[cp * n + c] : z2();
+        if (cp < rank) beta[cp * ld + perm[c]] = (c >= cp) ? Rm[cp * n + c] : z2();
+        S[t / n * ld + t % n] = z2();
     }
-    // S = Pi_r R11^{-1}: invert the r x r upper triangle column by column
-    for (int t = threadIdx.x; t < M_MAX * M_MAX; t += blockDim.x) Sg[t] = z2();
-    __syncthreads();
-    for (int c = threadIdx.x; c < r; c += blockDim.x) {
-        // solve R11 y = e_c (back substitution), y has entries 0..c
-        double2 y[M_MAX];
+    wsync();
+    // S = Pi_r R11^{-1}: lane c solves R11 y = e_c by back substitution
+    for (int c = threadIdx.x; c < rank; c += WS) {
         for (int i = c; i >= 0; --i) {
             double2 s = (i == c) ? make_double2(1.0, 0.0) : z2();
             for (int q = i + 1; q <= c; ++q) {
-                double2 a = Rm[i * n + q], b = y[q];
+                double2 a = Rm[i * n + q], b = S[perm[q] * ld + c];
                 s.x -= a.x * b.x - a.y * b.y;
                 s.y -= a.x * b.y + a.y * b.x;
             }
             double d = Rm[i * n + i].x;
-            y[i] = make_double2(s.x / d, s.y / d);
+            S[perm[i] * ld + c] = make_double2(s.x / d, s.y / d);
         }
-        for (int i = 0; i <= c; ++i) Sg[perm_s[i] * M_MAX + c] = y[i];
     }
-    __syncthreads();
-    return r;
+    wsync();
+    return rank;
+}
+
+__device__ inline void tile_ij(int t, int T, int herm, int* ti, int* tj) {
+    if (!herm) {
+        *ti = t / T;
+        *tj = t % T;
+        return;
+    }
+    int i = 0;
+    while (t >= T - i) {
+        t -= T - i;
+        ++i;
+    }
+    *ti = i;
+    *tj = i + t;
+}
+
+// Sum the per-CTA Gram partials ([tile][blk][36], fixed order) into G (ld,
+// hermitian fill when herm) and the |y|^2 diagonal; all threads of the CTA.
+// With reduced-precision storage the partials are FP32 (they carry FP32
+// accuracy) and are summed with compensated (Kahan) FP32 additions, which
+// cost far less than FP64 ones on GB300; FP64 storage sums in FP64.
+__device__ void reduce_partials(const double* __restrict__ part, int nblk, int nf_max, int herm, double2* G, int ld,
+                                double* diag, int fp64) {
+    const int T = (nf_max + 3) / 4;
+    const int ntiles = herm ? T * (T + 1) / 2 : T * T;
+    for (int u = threadIdx.x; u < ntiles * GSL; u += blockDim.x) {
+        const int tile = u / GSL, q = u % GSL;
+        const size_t off = (size_t)tile * nblk * GSL + q;
+        double s = 0.0;
+        if (fp64) {
+            const double* p = part + off;
+            for (int b = 0; b < nblk; ++b) s += p[(size_t)b * GSL];
+        } else {
+            const float* p = reinterpret_cast<const float*>(part) + off;
+            float sum = 0.f, comp = 0.f;
+            for (int b = 0; b < nblk; ++b) {
+                const float y = p[(size_t)b * GSL] - comp;
+                const float t = sum + y;
+                comp = (t - sum) - y;
+                sum = t;
+            }
+            s = (double)sum - (double)comp;
+        }
+        int ti, tj;
+        tile_ij(tile, T, herm, &ti, &tj);
+        if (q < 32) {
+            const int i = ti * 4 + ((q >> 1) >> 2), j = tj * 4 + ((q >> 1) & 3);
+            if (i < nf_max && j < nf_max) {
+                if (q & 1) {
+                    G[i * ld + j].y = s;
+                    if (herm && ti != tj) G[j * ld + i].y = -s;
+                } else {
+                    G[i * ld + j].x = s;
+                    if (herm && ti != tj) G[j * ld + i].x = s;
+                }
+            }
+        } else if (diag && ti == tj) {
+            const int j = tj * 4 + (q - 32);
+            if (j < nf_max) diag[j] = s;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
 // init: G0 = B^H B -> rank m_1, S0 (V_1 = B S0), rho = R Pi^T; U_{j,1} = rho
 __global__ void small_init_kernel(SmallState* ss, Ctl* ctl, const double2* __restrict__ G0,
-                                  const double* __restrict__ ref, int m, int s, double dtol, int wprec,
-                                  void* coefS_w) {
+                                  const double* __restrict__ ref, int m, int s, double dtol) {
     extern __shared__ __align__(16) unsigned char sm[];
     double2* G = (double2*)sm;
     double2* Rm = G + m * m;
-    int* perm = (int*)(Rm + m * m);
+    double2* S = Rm + m * m;
+    double2* rho = S + m * m;
+    int* perm = (int*)(rho + m * m);
     double* dd = (double*)(perm + M_MAX);
+    double* rf = dd + M_MAX;
     ld_mat(G, m, G0, m, m, m, m);
-    __syncthreads();
-    double2* rho = ss->sh.betan;              // r x m, permuted back
-    int r = pivoted_qr(G, m, m, ref, dtol, Rm, ss->sh.S, rho, perm, dd);
-    for (int j = 0; j < s; ++j) {
-        for (int t = threadIdx.x; t < M_MAX * M_MAX; t += blockDim.x) {
-            ss->sf[j].U[t] = rho[t];
-            ss->sf[j].Lam[t] = z2();
+    for (int i = threadIdx.x; i < m; i += WS) rf[i] = ref[i];
+    for (int t = threadIdx.x; t < m * m; t += WS) rho[t] = z2();
+    wsync();
+    const int r = pivoted_qr(G, m, m, rf, dtol, Rm, S, rho, perm, dd);
+    for (int t = threadIdx.x; t < M_MAX * M_MAX; t += WS) {
+        const int i = t / M_MAX, j = t % M_MAX;
+        ss->sh.S[t] = (i < m && j < m) ? S[i * m + j] : z2();
+        const double2 v = (i < r && j < m) ? rho[i * m + j] : z2();
+        for (int q = 0; q < s; ++q) {
+            ss->sf[q].U[t] = v;
+            ss->sf[q].Lam[t] = z2();
         }
-        for (int t = threadIdx.x; t < M_MAX; t += blockDim.x) ss->sf[j].conv[t] = 0;
-        if (threadIdx.x == 0) ss->sf[j].alive = 1;
     }
-    // coefficients of V_1 = B S0 in FP64 are read by init_basis from ss->sh.S
-    (void)wprec;
-    (void)coefS_w;
+    for (int q = 0; q < s; ++q) {
+        for (int t = threadIdx.x; t < M_MAX; t += WS) ss->sf[q].conv[t] = 0;
+        if (threadIdx.x == 0) ss->sf[q].alive = 1;
+    }
     if (threadIdx.x == 0) {
         ctl->k = 1;
         ctl->mk = r;
@@ -305,20 +350,24 @@ __global__ void small_init_kernel(SmallState* ss, Ctl* ctl, const double2* __res
     }
 }
 
-// alpha hermitised; coef_a = alpha, coef_bh = beta_k^H (work precision, M_MAX tiles)
-__global__ void small_alpha_kernel(SmallState* ss, const Ctl* __restrict__ ctl, const double2* __restrict__ alpha,
-                                   const double* __restrict__ yy, int wprec, void* coef_a, void* coef_bh) {
+// alpha_k from the Gram partials of V_k^H Y, hermitised; coef_a = alpha and
+// coef_bh = beta_k^H in the work precision (M_MAX tiles); ||y_i||^2
+__global__ void small_alpha_kernel(SmallState* ss, const Ctl* __restrict__ ctl, const double* __restrict__ part,
+                                   int nblk, int nf_max, int wprec, void* coef_a, void* coef_bh) {
     if (ctl->done) return;
+    __shared__ double2 A[M_MAX * M_MAX];
+    __shared__ double yy[M_MAX];
+    reduce_partials(part, nblk, nf_max, 0, A, M_MAX, yy, wprec == P64);
+    __syncthreads();
     const int mk_ = ctl->mk, mp = ctl->k > 1 ? ctl->mprev : 0;
     for (int t = threadIdx.x; t < M_MAX * M_MAX; t += blockDim.x) {
         int i = t / M_MAX, j = t % M_MAX;
         double2 v = z2();
         if (i < mk_ && j < mk_) {
-            double2 a = alpha[i * M_MAX + j], b = alpha[j * M_MAX + i];
+            double2 a = A[i * M_MAX + j], b = A[j * M_MAX + i];
             v = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
         }
         ss->sh.alpha[t] = v;
-        // beta_k^H (m_{k-1} x m_k): (beta^H)[i][j] = conj(beta_k[j][i])
         double2 bh = (i < mp && j < mk_) ? conjd(ss->sh.betak[j * M_MAX + i]) : z2();
         if (wprec == P64) {
             ((double2*)coef_a)[t] = v;
@@ -328,81 +377,86 @@ __global__ void small_alpha_kernel(SmallState* ss, const Ctl* __restrict__ ctl, 
             ((float2*)coef_bh)[t] = make_float2((float)bh.x, (float)bh.y);
         }
     }
-    for (int t = threadIdx.x; t < M_MAX; t += blockDim.x) ss->sh.yy[t] = yy[t];
+    for (int t = threadIdx.x; t < M_MAX; t += blockDim.x) ss->sh.yy[t] = t < mk_ ? yy[t] : 0.0;
 }
 
-// QR of W: G = W^H W -> m_{k+1}, S, beta_{k+1}
-__global__ void small_qr_kernel(SmallState* ss, Ctl* ctl, const double2* __restrict__ Gg, double dtol, int wprec,
-                                void* coefS_w) {
+// One block step's m x m work, one CTA per shift: reduce G = W^H W from the
+// partials, pivoted QR (every CTA computes the same deterministic result;
+// CTA 0 publishes S, beta_{k+1}, m_{k+1}), then this shift's recurrences.
+__global__ void small_step_kernel(SmallState* ss, Ctl* ctl, const double* __restrict__ part, int nblk, int m,
+                                  double dtol, const double* __restrict__ sigma, const double* __restrict__ target,
+                                  int freeze, int wprec, void* coefS_w, void* coefU_w, void* coefL_w, int* active,
+                                  int* conv_step, double* res_out, int MM) {
     if (ctl->done) return;
     extern __shared__ __align__(16) unsigned char sm[];
-    const int n = ctl->mk;
     double2* G = (double2*)sm;
-    double2* Rm = G + n * n;
-    int* perm = (int*)(Rm + n * n);
-    double* dd = (double*)(perm + M_MAX);
-    ld_mat(G, n, Gg, n, n, n, n);
-    __syncthreads();
-    int r = pivoted_qr(G, n, n, ss->sh.yy, dtol, Rm, ss->sh.S, ss->sh.betan, perm, dd);
-    __syncthreads();
-    if (wprec == P64) {
-        for (int t = threadIdx.x; t < M_MAX * M_MAX; t += blockDim.x) ((double2*)coefS_w)[t] = ss->sh.S[t];
-    } else {
+    double2* Rm = G + MM * MM;
+    double2* Bn = Rm + MM * MM;       // beta_{k+1} (mn x mk)
+    double2* S = Bn + MM * MM;        // mk x mn
+    double2* Dl = S + MM * MM;        // Delta -> Delta^{-1}
+    double2* T1 = Dl + MM * MM;
+    double2* Ut = T1 + MM * MM;
+    double2* LH = Ut + MM * MM;
+    double2* Cc = LH + MM * MM;
+    double2* col = Cc + MM * MM;
+    double* res = (double*)(col + MM);
+    double* dd = res + MM;
+    double* rf = dd + MM;
+    int* perm = (int*)(rf + MM);
+    const int j = blockIdx.x;
+    const int k = ctl->k, mk_ = ctl->mk, mp = k > 1 ? ctl->mprev : 0;
+    reduce_partials(part, nblk, m, 1, G, MM, nullptr, wprec == P64);
+    for (int i = threadIdx.x; i < mk_; i += blockDim.x) rf[i] = ss->sh.yy[i];
+    for (int t = threadIdx.x; t < MM * MM; t += blockDim.x) Bn[t] = z2();
+    __shared__ int mn_s;
+    bsync();
+    if (threadIdx.x < WS) {
+        const int r = pivoted_qr(G, MM, mk_, rf, dtol, Rm, S, Bn, perm, dd);
+        if (threadIdx.x == 0) mn_s = r;
+    }
+    bsync();
+    const int mn = mn_s;
+    if (j == 0) {
         for (int t = threadIdx.x; t < M_MAX * M_MAX; t += blockDim.x) {
-            double2 v = ss->sh.S[t];
-            ((float2*)coefS_w)[t] = make_float2((float)v.x, (float)v.y);
+            const int a = t / M_MAX, b = t % M_MAX;
+            const double2 sv = (a < mk_ && b < mn) ? S[a * MM + b] : z2();
+            ss->sh.S[t] = sv;
+            ss->sh.betan[t] = (a < mn && b < mk_) ? Bn[a * MM + b] : z2();
+            if (wprec == P64)
+                ((double2*)coefS_w)[t] = sv;
+            else
+                ((float2*)coefS_w)[t] = make_float2((float)sv.x, (float)sv.y);
+        }
+        if (threadIdx.x == 0) {
+            ctl->mnext = mn;
+            ctl->deflations += mk_ - mn;
         }
     }
-    if (threadIdx.x == 0) {
-        ctl->mnext = r;
-        ctl->deflations += n - r;
-    }
-}
-
-// per-shift recurrences; one CTA per shift
-__global__ void small_shift_kernel(SmallState* ss, Ctl* ctl, int m, const double* __restrict__ sigma,
-                                   const double* __restrict__ target, int freeze, int wprec, void* coefU_w,
-                                   void* coefL_w, int* active, int* conv_step, double* res_out, int MM) {
-    if (ctl->done) return;
-    const int j = blockIdx.x;
     SmallShift& sf = ss->sf[j];
-    const size_t tile = (size_t)M_MAX * M_MAX;
     if (!sf.alive) {
         if (threadIdx.x == 0) active[j] = 0;
         return;
     }
-    const int k = ctl->k, mk_ = ctl->mk, mp = k > 1 ? ctl->mprev : 0, mn = ctl->mnext;
-    extern __shared__ __align__(16) unsigned char sm[];
-    double2* Dl = (double2*)sm;                 // Delta -> its Cholesky factor (mk x mk)
-    double2* T1 = Dl + MM * MM;                 // scratch
-    double2* Ut = T1 + MM * MM;                 // Ut (mk x m)
-    double2* LH = Ut + MM * MM;                 // Lambda_{k+1}^H (mk x mn)
-    double2* Cc = LH + MM * MM;                 // C (mn x m), U_{k+1}
-    double* res = (double*)(Cc + MM * MM);
-    __shared__ int ok;
-
+    const size_t tile = (size_t)M_MAX * M_MAX;
+    const size_t cb = wprec == P64 ? 16 : 8;
     // Delta_k = alpha_k + sigma I - Lambda_k beta_k^H
     ld_mat(Dl, MM, ss->sh.alpha, mk_, mk_, mk_, mk_);
-    __syncthreads();
-    if (k > 1 && mp > 0) {
-        ld_mat(T1, MM, sf.Lam, mk_, mp, mk_, mp);
-        __syncthreads();
-        gemm(Dl, MM, T1, MM, 0, ss->sh.betak, M_MAX, 1, mk_, mp, mk_, -1.0, 1.0);
-    }
+    if (k > 1 && mp > 0) ld_mat(T1, MM, sf.Lam, mk_, mp, mk_, mp);
+    bsync();
+    if (k > 1 && mp > 0) gemm(Dl, MM, T1, MM, 0, ss->sh.betak, M_MAX, 1, mk_, mp, mk_, -1.0, 1.0);
     for (int i = threadIdx.x; i < mk_; i += blockDim.x) Dl[i * MM + i].x += sigma[j];
-    // keep Delta exactly hermitian
-    for (int t = threadIdx.x; t < mk_ * mk_; t += blockDim.x) {
+    bsync();
+    for (int t = threadIdx.x; t < mk_ * mk_; t += blockDim.x) {      // exact hermitian symmetry
         int a = t / mk_, b = t % mk_;
         if (b < a) {
             double2 lo = Dl[a * MM + b], up = Dl[b * MM + a];
-            Dl[a * MM + b] = make_double2(0.5 * (lo.x + up.x), 0.5 * (lo.y - up.y));
+            double2 h = make_double2(0.5 * (lo.x + up.x), 0.5 * (lo.y - up.y));
+            Dl[a * MM + b] = h;
+            Dl[b * MM + a] = conjd(h);
         }
     }
-    __syncthreads();
-    int c_ok = chol(Dl, MM, mk_);
-    if (threadIdx.x == 0) ok = c_ok;
-    __syncthreads();
-    if (!ok) {
+    bsync();
+    if (!gj_inverse(Dl, MM, mk_, col)) {
         if (threadIdx.x == 0) {
             atomicExch(&ctl->status, ST_NOT_HPD);
             active[j] = 0;
@@ -410,44 +464,34 @@ __global__ void small_shift_kernel(SmallState* ss, Ctl* ctl, int m, const double
         }
         return;
     }
-    // Ut = Delta^{-1} U_k
-    ld_mat(Ut, MM, sf.U, mk_, m, mk_, m);
-    __syncthreads();
-    chol_solve(Dl, MM, mk_, Ut, MM, m);
-    // Lambda_{k+1}^H = Delta^{-1} beta_{k+1}^H
-    for (int t = threadIdx.x; t < mk_ * mn; t += blockDim.x) {
-        int a = t / mn, c = t % mn;
-        LH[a * MM + c] = conjd(ss->sh.betan[c * M_MAX + a]);
-    }
-    __syncthreads();
-    chol_solve(Dl, MM, mk_, LH, MM, mn);
-    // C = -beta_{k+1} Ut  (mn x m); residual norms
-    gemm(Cc, MM, ss->sh.betan, M_MAX, 0, Ut, MM, 0, mn, mk_, m, -1.0, 0.0);
+    // Ut = Delta^{-1} U_k (mk x m); Lambda_{k+1}^H = Delta^{-1} beta_{k+1}^H (mk x mn)
+    ld_mat(T1, MM, sf.U, mk_, m, mk_, m);
+    bsync();
+    gemm(Ut, MM, Dl, MM, 0, T1, MM, 0, mk_, mk_, m, 1.0, 0.0);
+    gemm(LH, MM, Dl, MM, 0, Bn, MM, 1, mk_, mk_, mn, 1.0, 0.0);
+    // C = -beta_{k+1} Ut (mn x m) gives the residual estimates, and it is also
+    // U_{k+1} = -Lambda_{k+1} U_k = -beta_{k+1} Delta_k^{-1} U_k
+    gemm(Cc, MM, Bn, MM, 0, Ut, MM, 0, mn, mk_, m, -1.0, 0.0);
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
         double s2 = 0.0;
         for (int c = 0; c < mn; ++c) s2 += Cc[c * MM + i].x * Cc[c * MM + i].x + Cc[c * MM + i].y * Cc[c * MM + i].y;
         res[i] = sqrt(s2);
     }
-    __syncthreads();
-    // coefficients for the shift update: Ut with columns frozen before this step zeroed
+    bsync();
+    // shift-update coefficients: Ut with the columns frozen before this step zeroed
     for (int t = threadIdx.x; t < mk_ * m; t += blockDim.x) {
         int a = t / m, i = t % m;
         if (freeze && sf.conv[i]) Ut[a * MM + i] = z2();
     }
-    __syncthreads();
-    st_mat_work(wprec, (char*)coefU_w + (size_t)j * tile * (wprec == P64 ? 16 : 8), Ut, MM, mk_, m);
-    st_mat_work(wprec, (char*)coefL_w + (size_t)j * tile * (wprec == P64 ? 16 : 8), LH, MM, mk_, mn);
-    // U_{k+1} = -Lambda_{k+1} U_k = -(LH)^H U_k  (mn x m), into Cc
-    ld_mat(T1, MM, sf.U, mk_, m, mk_, m);
-    __syncthreads();
-    gemm(Cc, MM, LH, MM, 1, T1, MM, 0, mn, mk_, m, -1.0, 0.0);
-    // store Lambda_{k+1} = LH^H (mn x mk), U_{k+1}
+    bsync();
+    st_mat_work(wprec, (char*)coefU_w + (size_t)j * tile * cb, Ut, MM, mk_, m);
+    st_mat_work(wprec, (char*)coefL_w + (size_t)j * tile * cb, LH, MM, mk_, mn);
     for (int t = threadIdx.x; t < M_MAX * M_MAX; t += blockDim.x) {
         int c = t / M_MAX, a = t % M_MAX;
         sf.Lam[t] = (c < mn && a < mk_) ? conjd(LH[a * MM + c]) : z2();
         sf.U[t] = (c < mn && a < m) ? Cc[c * MM + a] : z2();
     }
-    __syncthreads();
+    bsync();
     if (threadIdx.x == 0) {
         int any_before = 0, any_after = 0;
         for (int i = 0; i < m; ++i) {
@@ -460,8 +504,7 @@ __global__ void small_shift_kernel(SmallState* ss, Ctl* ctl, int m, const double
             if (!sf.conv[i]) any_after = 1;
         }
         active[j] = freeze ? any_before : 1;
-        sf.alive = any_after || !freeze;
-        if (!freeze && !any_after) sf.alive = 0;
+        sf.alive = any_after;
     }
 }
 
@@ -492,38 +535,33 @@ __global__ void small_finish_kernel(SmallState* ss, Ctl* ctl, int s, int m, cons
     }
 }
 
+size_t step_smem(int MM) { return 9 * (size_t)MM * MM * sizeof(double2) + MM * sizeof(double2) + 3 * MM * sizeof(double) + M_MAX * sizeof(int); }
+
 }  // namespace
 
 void launch_small_init(SmallState* ss, Ctl* ctl, const double2* G0, const double* ref, int m, int s, double dtol,
-                       int wprec, void* coefS_w, cudaStream_t st) {
-    size_t sm = 2 * (size_t)m * m * sizeof(double2) + M_MAX * sizeof(int) + M_MAX * sizeof(double);
-    small_init_kernel<<<1, NT, sm, st>>>(ss, ctl, G0, ref, m, s, dtol, wprec, coefS_w);
+                       cudaStream_t st) {
+    size_t sm = 4 * (size_t)m * m * sizeof(double2) + M_MAX * sizeof(int) + 2 * M_MAX * sizeof(double);
+    small_init_kernel<<<1, WS, sm, st>>>(ss, ctl, G0, ref, m, s, dtol);
 }
 
-void launch_small_alpha(SmallState* ss, const Ctl* ctl, const double2* alpha, const double* yy, int wprec,
+void launch_small_alpha(SmallState* ss, const Ctl* ctl, const double* partials, int nblk, int nf_max, int wprec,
                         void* coef_a, void* coef_bh, cudaStream_t st) {
-    small_alpha_kernel<<<1, 256, 0, st>>>(ss, ctl, alpha, yy, wprec, coef_a, coef_bh);
+    small_alpha_kernel<<<1, 256, 0, st>>>(ss, ctl, partials, nblk, nf_max, wprec, coef_a, coef_bh);
 }
 
-void launch_small_qr(SmallState* ss, Ctl* ctl, const double2* G, double dtol, int wprec, void* coefS_w,
-                     cudaStream_t st) {
-    size_t sm = 2 * (size_t)M_MAX * M_MAX * sizeof(double2) + M_MAX * sizeof(int) + M_MAX * sizeof(double);
-    small_qr_kernel<<<1, NT, sm, st>>>(ss, ctl, G, dtol, wprec, coefS_w);
-}
-
-void launch_small_shift(SmallState* ss, Ctl* ctl, int s, int m, const double* sigma_dev, const double* target_dev,
-                        int freeze, int wprec, void* coefU_w, void* coefL_w, int* active, int* conv_step,
-                        double* res_out, cudaStream_t st) {
-    int MM = m;                        // block widths never exceed the initial width m
-    size_t sm = 5 * (size_t)MM * MM * sizeof(double2) + M_MAX * sizeof(double);
+void launch_small_step(SmallState* ss, Ctl* ctl, const double* partials, int nblk, int s, int m, double dtol,
+                       const double* sigma_dev, const double* target_dev, int freeze, int wprec, void* coefS_w,
+                       void* coefU_w, void* coefL_w, int* active, int* conv_step, double* res_out,
+                       cudaStream_t st) {
+    const int MM = m;                  // block widths never exceed the initial width m
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(small_shift_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(5 * M_MAX * M_MAX * sizeof(double2) + M_MAX * sizeof(double)));
+        cudaFuncSetAttribute(small_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step_smem(M_MAX));
         attr_set = true;
     }
-    small_shift_kernel<<<s, NT, sm, st>>>(ss, ctl, m, sigma_dev, target_dev, freeze, wprec, coefU_w, coefL_w,
-                                          active, conv_step, res_out, MM);
+    small_step_kernel<<<s, NT, step_smem(MM), st>>>(ss, ctl, partials, nblk, m, dtol, sigma_dev, target_dev, freeze,
+                                                    wprec, coefS_w, coefU_w, coefL_w, active, conv_step, res_out, MM);
 }
 
 void launch_small_finish(SmallState* ss, Ctl* ctl, int s, int m, const int* active, cudaStream_t st) {

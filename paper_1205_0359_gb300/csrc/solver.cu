@@ -68,6 +68,7 @@ struct dsbcg_ctx {
         void *vring = nullptr, *zw = nullptr, *y = nullptr;       // storage precision
         void *P = nullptr, *Xin = nullptr;                        // work precision
         double2 *B64 = nullptr, *X64 = nullptr, *R64 = nullptr, *T64a = nullptr, *T64b = nullptr, *rhs = nullptr;
+        double2 *Xg = nullptr, *Bg = nullptr;
         double* partials = nullptr;
         double* rpart = nullptr;
         SmallState* ss = nullptr;
@@ -167,6 +168,8 @@ dsbcg_status ensure_ws(dsbcg_ctx* c, int m, int s, int prec) {
     CKS(dmalloc(c, (void**)&w.T64a, m * db));
     CKS(dmalloc(c, (void**)&w.T64b, m * db));
     CKS(dmalloc(c, (void**)&w.rhs, m * db));
+    CKS(dmalloc(c, (void**)&w.Xg, m * db));
+    CKS(dmalloc(c, (void**)&w.Bg, m * db));
     w.nblk = gram_blocks(c->n, m);
     CKS(dmalloc(c, (void**)&w.partials, gram_partial_doubles(M_MAX) * sizeof(double)));
     w.rblk = residual_blocks(c->n);
@@ -305,7 +308,7 @@ dsbcg_status inner_solve(dsbcg_ctx* c, const double2* rhs, int m_in, const doubl
     {
         Prof p(c, DSBCG_KCLASS_SMALL, 2);
         launch_gram_reduce(w.partials, w.nblk, m_in, 1, 1, w.G, w.diag, nullptr, m_in, c->st);
-        launch_small_init(w.ss, w.ctl, w.G, w.diag, m_in, s_in, dtol, wp, w.coefS, c->st);
+        launch_small_init(w.ss, w.ctl, w.G, w.diag, m_in, s_in, dtol, c->st);
     }
     char* ring = (char*)w.vring;
     {
@@ -339,9 +342,8 @@ dsbcg_status inner_solve(dsbcg_ctx* c, const double2* rhs, int m_in, const doubl
                 launch_gram(prec, Vk, w.y, ld, n, w.ctl, 0, m_in, 0, 1, w.partials, w.nblk, c->hscale, c->st);
             }
             {
-                Prof p(c, DSBCG_KCLASS_SMALL, 2);
-                launch_gram_reduce(w.partials, w.nblk, m_in, 0, 1, w.alpha, w.yy, w.ctl, 0, c->st);
-                launch_small_alpha(w.ss, w.ctl, w.alpha, w.yy, wp, w.coef_a, w.coef_bh, c->st);
+                Prof p(c, DSBCG_KCLASS_SMALL);
+                launch_small_alpha(w.ss, w.ctl, w.partials, w.nblk, m_in, wp, w.coef_a, w.coef_bh, c->st);
             }
             {
                 Prof p(c, DSBCG_KCLASS_UPDATE);
@@ -353,11 +355,9 @@ dsbcg_status inner_solve(dsbcg_ctx* c, const double2* rhs, int m_in, const doubl
                 launch_gram(prec, w.zw, w.zw, ld, n, w.ctl, 0, m_in, 1, 0, w.partials, w.nblk, c->hscale, c->st);
             }
             {
-                Prof p(c, DSBCG_KCLASS_SMALL, 3);
-                launch_gram_reduce(w.partials, w.nblk, m_in, 1, 0, w.G, w.diag, w.ctl, 0, c->st);
-                launch_small_qr(w.ss, w.ctl, w.G, dtol, wp, w.coefS, c->st);
-                launch_small_shift(w.ss, w.ctl, s_in, m_in, w.sigma, w.target, freeze, wp, w.coefU, w.coefL,
-                                   w.active, w.conv_step, w.res, c->st);
+                Prof p(c, DSBCG_KCLASS_SMALL);
+                launch_small_step(w.ss, w.ctl, w.partials, w.nblk, s_in, m_in, dtol, w.sigma, w.target, freeze, wp,
+                                  w.coefS, w.coefU, w.coefL, w.active, w.conv_step, w.res, c->st);
             }
             {
                 Prof p(c, DSBCG_KCLASS_SHIFT);
@@ -654,45 +654,41 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
         deflations += ir.deflations;
         final_rank = ir.final_rank;
         if (ir.status == DSBCG_ERR_NOT_HPD) return DSBCG_ERR_NOT_HPD;
+        if (ir.status != 0) return DSBCG_ERR_CUDA;
         Prof p(c, DSBCG_KCLASS_OTHER);
         launch_accumulate(work_prec(prec), w.X64, ld, w.Xin, ld, s * m, n, c->st);
     }
-    // --- FP64 true residuals
+    // --- FP64 true residuals and per-shift restarts.  Shift by shift: R_j of
+    // every column; while some column of shift j is above tol, restart on the
+    // unconverged columns of R_j, then recompute the residual of just those
+    // columns, which is the right-hand side of the next restart.
     std::vector<double> r2(m);
-    for (int j = 0; j < s; ++j) {
-        CKS(true_residual(c, w.R64, w.B64, w.X64 + (size_t)j * m * ld, m, sigma[j], r2.data()));
-        mvms += m;
-        for (int i = 0; i < m; ++i) rel[(size_t)j * m + i] = bn[i] > 0 ? sqrt(r2[i]) / bn[i] : 0.0;
-    }
-    // --- per-shift restarts on the true residual
-    auto unconverged = [&](int j, std::vector<int>& cols) {
-        cols.clear();
-        for (int i = 0; i < m; ++i)
-            if (rel[(size_t)j * m + i] > tol) cols.push_back(i);
+    std::vector<int> cols, pos(m);
+    auto gather = [&](double2* dst, const double2* src, const std::vector<int>& idx) -> dsbcg_status {
+        for (size_t q = 0; q < idx.size(); ++q)
+            CK(cudaMemcpyAsync(dst + q * ld, src + (size_t)idx[q] * ld, db, cudaMemcpyDeviceToDevice, c->st));
+        return DSBCG_OK;
     };
-    std::vector<int> cols;
-    bool any = false;
     for (int j = 0; j < s; ++j) {
-        unconverged(j, cols);
-        if (!cols.empty()) any = true;
-    }
-    while (any && prm.refine && restarts < prm.max_restarts && total_steps < prm.max_block_steps) {
-        any = false;
-        for (int j = 0; j < s && restarts < prm.max_restarts; ++j) {
-            unconverged(j, cols);
-            if (cols.empty()) continue;
-            double2* Xj = w.X64 + (size_t)j * m * ld;
-            // recompute R_j (all columns) and gather the unconverged ones
-            CKS(true_residual(c, w.R64, w.B64, Xj, m, sigma[j], r2.data()));
-            mvms += m;
+        double2* Xj = w.X64 + (size_t)j * m * ld;
+        CKS(true_residual(c, w.R64, w.B64, Xj, m, sigma[j], r2.data()));
+        mvms += m;
+        cols.clear();
+        for (int i = 0; i < m; ++i) {
+            rel[(size_t)j * m + i] = bn[i] > 0 ? sqrt(r2[i]) / bn[i] : 0.0;
+            pos[i] = i;
+            if (rel[(size_t)j * m + i] > tol) cols.push_back(i);
+        }
+        while (!cols.empty() && prm.refine && restarts < prm.max_restarts && total_steps < prm.max_block_steps) {
             const int mu = (int)cols.size();
             std::vector<double> tg(mu);
+            std::vector<int> src(mu);
             for (int q = 0; q < mu; ++q) {
-                int i = cols[q];
-                CK(cudaMemcpyAsync(w.rhs + (size_t)q * ld, w.R64 + (size_t)i * ld, db, cudaMemcpyDeviceToDevice, c->st));
-                double ri = sqrt(r2[i]);
-                tg[q] = std::max(drop * ri, 0.5 * tol * bn[i]);
+                src[q] = pos[cols[q]];
+                const int i = cols[q];
+                tg[q] = std::max(drop * rel[(size_t)j * m + i] * bn[i], 0.5 * tol * bn[i]);
             }
+            CKS(gather(w.rhs, w.R64, src));
             InnerResult ir;
             CKS(inner_solve(c, w.rhs, mu, &sigma[j], 1, tg.data(), prec, dtol,
                             std::max(1, prm.max_block_steps - total_steps), prm.freeze_converged, prm.poll_every,
@@ -702,17 +698,26 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
             deflations += ir.deflations;
             restarts += 1;
             if (ir.status == DSBCG_ERR_NOT_HPD) return DSBCG_ERR_NOT_HPD;
+            if (ir.status != 0) return DSBCG_ERR_CUDA;
             for (int q = 0; q < mu; ++q) {
+                if (conv_tmp[q] >= 0) conv[(size_t)j * m + cols[q]] = conv_tmp[q];
                 Prof p(c, DSBCG_KCLASS_OTHER);
                 launch_accumulate(work_prec(prec), Xj + (size_t)cols[q] * ld, ld,
                                   (char*)w.Xin + (size_t)q * ld * prec_elem_bytes(work_prec(prec)), ld, 1, n, c->st);
-                if (conv_tmp[q] >= 0) conv[(size_t)j * m + cols[q]] = conv_tmp[q];
             }
-            CKS(true_residual(c, w.R64, w.B64, Xj, m, sigma[j], r2.data()));
-            mvms += m;
-            for (int i = 0; i < m; ++i) rel[(size_t)j * m + i] = bn[i] > 0 ? sqrt(r2[i]) / bn[i] : 0.0;
-            unconverged(j, cols);
-            if (!cols.empty()) any = true;
+            // residual of the restarted columns only
+            CKS(gather(w.Xg, Xj, cols));
+            CKS(gather(w.Bg, w.B64, cols));
+            CKS(true_residual(c, w.R64, w.Bg, w.Xg, mu, sigma[j], r2.data()));
+            mvms += mu;
+            std::vector<int> next;
+            for (int q = 0; q < mu; ++q) {
+                const int i = cols[q];
+                rel[(size_t)j * m + i] = bn[i] > 0 ? sqrt(r2[q]) / bn[i] : 0.0;
+                pos[i] = q;
+                if (rel[(size_t)j * m + i] > tol) next.push_back(i);
+            }
+            cols.swap(next);
         }
     }
     for (double r : rel)
