@@ -300,171 +300,148 @@ __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bu
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// rows per CTA: the double-buffered tiles take <= 80 KB of shared memory so
-// that 2-3 CTAs (and their compute phases) overlap on each SM
-template <int NF, int PW>
-__host__ __device__ constexpr int su_rows() {
-    return (NF * (int)sizeof(typename Tr<PW>::S2) * 128 * 5 <= 81920) ? 128 : 64;
-}
-template <int NF, int PW>
-__host__ __device__ constexpr size_t su_smem_bytes() {
-    return (size_t)5 * NF * su_rows<NF, PW>() * sizeof(typename Tr<PW>::S2)      // V tile + 2 x (P, X)
-           + (size_t)3 * NF * NF * sizeof(typename Tr<PW>::C) + 2 * sizeof(uint64_t) + 16;
-}
-
-template <int P, int PW, int NF, int ROWS>
-__global__ void __launch_bounds__(ROWS) shift_update_kernel(
-    typename Tr<P>::S2* __restrict__ Vn, const typename Tr<P>::S2* __restrict__ W,
-    const typename Tr<P>::S2* __restrict__ Vk, size_t ld, typename Tr<PW>::S2* __restrict__ Pb,
-    typename Tr<PW>::S2* __restrict__ Xb, size_t ldw, size_t n, int s, int m, Ctl* __restrict__ ctl,
-    const typename Tr<PW>::C* __restrict__ cS, const typename Tr<PW>::C* __restrict__ cU,
-    const typename Tr<PW>::C* __restrict__ cL, const int* __restrict__ active, float hscale) {
+// V_{k+1} = W S (one thread per row; W and V in the storage precision)
+template <int P, int NF>
+__global__ void __launch_bounds__(256) v_update_kernel(typename Tr<P>::S2* __restrict__ Vn,
+                                                       const typename Tr<P>::S2* __restrict__ W, size_t ld,
+                                                       size_t n, const Ctl* __restrict__ ctl,
+                                                       const typename Tr<(P == P64 ? P64 : P32)>::C* __restrict__ cS,
+                                                       float hscale) {
+    constexpr int PW = (P == P64) ? P64 : P32;
     using C = typename Tr<PW>::C;
     using R = typename Tr<PW>::R;
-    using E = typename Tr<PW>::S2;          // work-precision storage element (float2 / double2)
     if (ctl->done) return;
-    const int mk_ = ctl->mk, mn = ctl->mnext, k = ctl->k;
-    extern __shared__ __align__(128) unsigned char su_smem[];
-    E* sV = reinterpret_cast<E*>(su_smem);                    // [NF][ROWS]
-    E* sP[2] = {sV + NF * ROWS, sV + 3 * NF * ROWS};          // [NF][ROWS] each
-    E* sX[2] = {sV + 2 * NF * ROWS, sV + 4 * NF * ROWS};
-    C* sS = reinterpret_cast<C*>(sV + 5 * NF * ROWS);
-    C* sU = sS + NF * NF;
-    C* sL = sU + NF * NF;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sL + NF * NF);
-    const int tid = threadIdx.x;
-    const size_t e0 = (size_t)blockIdx.x * ROWS;
-    const int rows = (int)((n - e0) < (size_t)ROWS ? (n - e0) : (size_t)ROWS);
-    const uint32_t tile_bytes = (uint32_t)rows * sizeof(E);
-    const bool live = tid < rows;
-    const size_t e = e0 + tid;
+    const int mk_ = ctl->mk, mn = ctl->mnext;
+    __shared__ C sS[NF * NF];
+    for (int t = threadIdx.x; t < NF * NF; t += blockDim.x) sS[t] = cS[(t / NF) * M_MAX + (t % NF)];
+    __syncthreads();
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
     const float inv = (P == PBF16 || P == PF16) ? 1.f / hscale : 1.f;
     const float scl = (P == PBF16 || P == PF16) ? hscale : 1.f;
-
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        mbar_fence_init();
-    }
-    for (int t = tid; t < NF * NF; t += ROWS) sS[t] = cS[(t / NF) * M_MAX + (t % NF)];
-    __syncthreads();
-
-    // V_{k+1} = W S into the shared tile (and to HBM)
-    if (live) {
-        C w[NF];
+    C w[NF];
 #pragma unroll
-        for (int a = 0; a < NF; ++a) {
-            if (a < mk_) {
-                auto q = Elem<P>::ld(W + (size_t)a * ld, e, inv);
-                w[a] = mk(R(q.x), R(q.y));
-            } else {
-                w[a] = mk(R(0), R(0));
-            }
+    for (int a = 0; a < NF; ++a) {
+        if (a < mk_) {
+            auto q = Elem<P>::ld(W + (size_t)a * ld, e, inv);
+            w[a] = mk(R(q.x), R(q.y));
+        } else {
+            w[a] = mk(R(0), R(0));
         }
+    }
 #pragma unroll
-        for (int c = 0; c < NF; ++c) {
+    for (int c = 0; c < NF; ++c) {
+        if (c < mn) {
             C acc = mk(R(0), R(0));
 #pragma unroll
             for (int a = 0; a < NF; ++a) cfma(acc, w[a], sS[a * NF + c]);
-            sV[c * ROWS + tid] = acc;
-            if (c < mn) Elem<P>::st(Vn + (size_t)c * ld, e, mk((typename Tr<P>::R)acc.x, (typename Tr<P>::R)acc.y), scl);
+            Elem<P>::st(Vn + (size_t)c * ld, e, mk((typename Tr<P>::R)acc.x, (typename Tr<P>::R)acc.y), scl);
         }
     }
+}
 
-    // tiles of shift j into buffer b (issued by thread 0)
-    auto issue = [&](int j, int b) {
-        const uint32_t np = (k > 1) ? (uint32_t)mk_ : 0u;
-        mbar_expect_tx(&bar[b], (np + (uint32_t)m) * tile_bytes);
-        const E* Pj = Pb + (size_t)j * m * ldw + e0;
-        const E* Xj = Xb + (size_t)j * m * ldw + e0;
-        for (uint32_t f = 0; f < np; ++f) bulk_g2s(sP[b] + f * ROWS, Pj + f * ldw, tile_bytes, &bar[b]);
-        for (int i = 0; i < m; ++i) bulk_g2s(sX[b] + i * ROWS, Xj + (size_t)i * ldw, tile_bytes, &bar[b]);
-    };
+// Per-shift update of one row tile: X_j += P_j Ut_j, P_j <- V_{k+1} - P_j Lh_j.
+// One CTA per (row tile, shift), shift index fastest so that the CTAs that
+// read the same V_{k+1} tile run together and share it through L2.  The
+// tiles of V_{k+1}, P_j and X_j (one contiguous run of ROWS elements per
+// field) arrive in shared memory by bulk asynchronous copies completing on
+// one mbarrier; many small independent CTAs per SM overlap their copies and
+// their arithmetic.  Results are stored directly (coalesced).  The mbarrier
+// wait is bounded: on timeout the CTA records an error in the control block
+// and returns after draining its copies.  At k == 1 the search block is
+// P_j = V_1 (the current block, storage precision).
+template <int NF, int PW, int PS>
+__host__ __device__ constexpr size_t su_smem_bytes(int rows) {
+    return (size_t)rows * NF * (sizeof(typename Tr<PS>::S2) + 2 * sizeof(typename Tr<PW>::S2))
+           + 2 * (size_t)NF * NF * sizeof(typename Tr<PW>::C) + 16;
+}
 
-    // every thread walks the same list of active shifts, so the pending and
-    // phase bookkeeping below is identical in all threads
-    int next = 0;
-    while (next < s && !active[next]) ++next;
-    uint32_t phase[2] = {0u, 0u};
-    bool pend[2] = {false, false};
-    if (next < s) {
-        if (tid == 0) issue(next, 0);
-        pend[0] = true;
-    }
-    bool ok = true;
-    for (int q = 0; next < s; ++q) {
-        const int j = next;
-        const int b = q & 1;
-        next = j + 1;
-        while (next < s && !active[next]) ++next;
-        if (next < s) {
-            if (tid == 0) {
-                bulk_wait_read_all();      // buffer b^1 may still be read by the previous shift's stores
-                issue(next, b ^ 1);
-            }
-            pend[b ^ 1] = true;
-        }
-        for (int t = tid; t < NF * NF; t += ROWS) {
-            sU[t] = cU[((size_t)j * M_MAX + t / NF) * M_MAX + t % NF];
-            sL[t] = cL[((size_t)j * M_MAX + t / NF) * M_MAX + t % NF];
-        }
-        if (mbar_wait(&bar[b], phase[b])) {
-            phase[b] ^= 1u;
-            pend[b] = false;
-        } else {
-            ok = false;
-        }
-        __syncthreads();
-        if (!__syncthreads_and(ok)) break;
-        if (live) {
-            C t[NF], x[NF];
-#pragma unroll
-            for (int a = 0; a < NF; ++a) {
-                if (a < mk_) {
-                    if (k == 1) {
-                        auto v = Elem<P>::ld(Vk + (size_t)a * ld, e, inv);
-                        t[a] = mk(R(v.x), R(v.y));
-                    } else {
-                        t[a] = sP[b][a * ROWS + tid];
-                    }
-                } else {
-                    t[a] = mk(R(0), R(0));
-                }
-                x[a] = a < m ? sX[b][a * ROWS + tid] : mk(R(0), R(0));
-            }
-#pragma unroll
-            for (int i = 0; i < NF; ++i) {
-#pragma unroll
-                for (int a = 0; a < NF; ++a) cfma(x[i], t[a], sU[a * NF + i]);
-                if (i < m) sX[b][i * ROWS + tid] = x[i];
-            }
-#pragma unroll
-            for (int c = 0; c < NF; ++c) {
-                if (c < mn) {
-                    C p = sV[c * ROWS + tid];
-#pragma unroll
-                    for (int a = 0; a < NF; ++a) cfms(p, t[a], sL[a * NF + c]);
-                    sP[b][c * ROWS + tid] = p;
-                }
-            }
-        }
-        fence_proxy_async();               // generic-proxy smem writes -> bulk stores
-        __syncthreads();
-        if (tid == 0) {
-            E* Pj = Pb + (size_t)j * m * ldw + e0;
-            E* Xj = Xb + (size_t)j * m * ldw + e0;
-            for (int c = 0; c < mn; ++c) bulk_s2g(Pj + (size_t)c * ldw, sP[b] + c * ROWS, tile_bytes);
-            for (int i = 0; i < m; ++i) bulk_s2g(Xj + (size_t)i * ldw, sX[b] + i * ROWS, tile_bytes);
-            bulk_commit();
-        }
-    }
+template <int P, int PW, int NF, int ROWS>
+__global__ void __launch_bounds__(ROWS) shift_tile_kernel(
+    const typename Tr<P>::S2* __restrict__ Vn, const typename Tr<P>::S2* __restrict__ Vk, size_t ld,
+    typename Tr<PW>::S2* __restrict__ Pb, typename Tr<PW>::S2* __restrict__ Xb, size_t ldw, size_t n, int s, int m,
+    Ctl* __restrict__ ctl, const typename Tr<PW>::C* __restrict__ cU, const typename Tr<PW>::C* __restrict__ cL,
+    const int* __restrict__ active, float hscale) {
+    using C = typename Tr<PW>::C;
+    using R = typename Tr<PW>::R;
+    using E = typename Tr<PW>::S2;
+    using SE = typename Tr<P>::S2;
+    if (ctl->done) return;
+    const int j = (int)(blockIdx.x % (unsigned)s);
+    if (!active[j]) return;
+    const int mk_ = ctl->mk, mn = ctl->mnext, k = ctl->k;
+    extern __shared__ __align__(128) unsigned char su_smem[];
+    SE* sV = reinterpret_cast<SE*>(su_smem);                        // [NF][ROWS] V_{k+1} (or V_1 at k == 1)
+    E* sP = reinterpret_cast<E*>(su_smem + (size_t)NF * ROWS * sizeof(SE));
+    E* sX = sP + NF * ROWS;
+    C* sU = reinterpret_cast<C*>(sX + NF * ROWS);
+    C* sL = sU + NF * NF;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sL + NF * NF);
+    const int tid = threadIdx.x;
+    const size_t e0 = (size_t)(blockIdx.x / (unsigned)s) * ROWS;
+    const int rows = (int)((n - e0) < (size_t)ROWS ? (n - e0) : (size_t)ROWS);
+    const uint32_t tb = (uint32_t)rows * sizeof(E), tbs = (uint32_t)rows * sizeof(SE);
+    const E* Pj = Pb + (size_t)j * m * ldw + e0;
+    E* Pjw = Pb + (size_t)j * m * ldw + e0;
+    E* Xj = Xb + (size_t)j * m * ldw + e0;
     if (tid == 0) {
-        bulk_wait_all();
-        if (!ok) {
-            // drain loads still in flight into either buffer (bounded), then report
-            for (int bb = 0; bb < 2; ++bb)
-                if (pend[bb]) mbar_wait(&bar[bb], phase[bb]);
+        mbar_init(bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // k == 1: the search block is V_1 itself (loaded into sP's place via sV below)
+        const uint32_t nv = (uint32_t)mn + (k == 1 ? (uint32_t)mk_ : 0u);
+        const uint32_t np = k > 1 ? (uint32_t)mk_ : 0u;
+        mbar_expect_tx(bar, nv * tbs + (np + (uint32_t)m) * tb);
+        for (int c = 0; c < mn; ++c) bulk_g2s(sV + c * ROWS, Vn + (size_t)c * ld + e0, tbs, bar);
+        if (k == 1) {
+            // V_1 (storage precision) into the P tile's space, which is at least as large
+            for (int a = 0; a < mk_; ++a) bulk_g2s(reinterpret_cast<SE*>(sP) + a * ROWS, Vk + (size_t)a * ld + e0, tbs, bar);
+        } else {
+            for (int a = 0; a < mk_; ++a) bulk_g2s(sP + a * ROWS, Pj + (size_t)a * ldw, tb, bar);
+        }
+        for (int i = 0; i < m; ++i) bulk_g2s(sX + i * ROWS, Xj + (size_t)i * ldw, tb, bar);
+    }
+    for (int t = tid; t < NF * NF; t += ROWS) {
+        sU[t] = cU[((size_t)j * M_MAX + t / NF) * M_MAX + t % NF];
+        sL[t] = cL[((size_t)j * M_MAX + t / NF) * M_MAX + t % NF];
+    }
+    const bool ok = mbar_wait(bar, 0);
+    __syncthreads();
+    if (!__syncthreads_and(ok)) {
+        if (tid == 0) {
+            mbar_wait(bar, 0);
             atomicExch(&ctl->status, ST_WAIT_TIMEOUT);
+        }
+        return;
+    }
+    if (tid >= rows) return;
+    const float inv = (P == PBF16 || P == PF16) ? 1.f / hscale : 1.f;
+    auto ldv = [&](const SE* base, int c) -> C {
+        auto q = Elem<P>::ld(base, (size_t)c * ROWS + tid, inv);
+        return mk(R(q.x), R(q.y));
+    };
+    C t[NF], x[NF];
+#pragma unroll
+    for (int a = 0; a < NF; ++a) {
+        if (a < mk_) t[a] = (k == 1) ? ldv(reinterpret_cast<const SE*>(sP), a) : sP[a * ROWS + tid];
+        else t[a] = mk(R(0), R(0));
+        x[a] = a < m ? sX[a * ROWS + tid] : mk(R(0), R(0));
+    }
+#pragma unroll
+    for (int i = 0; i < NF; ++i) {
+#pragma unroll
+        for (int a = 0; a < NF; ++a) cfma(x[i], t[a], sU[a * NF + i]);
+        if (i < m) Xj[(size_t)i * ldw + tid] = x[i];
+    }
+#pragma unroll
+    for (int c = 0; c < NF; ++c) {
+        if (c < mn) {
+            C p = ldv(sV, c);
+#pragma unroll
+            for (int a = 0; a < NF; ++a) cfms(p, t[a], sL[a * NF + c]);
+            Pjw[(size_t)c * ldw + tid] = p;
         }
     }
 }
@@ -516,18 +493,20 @@ void launch_su_t(void* Vnext, const void* W, const void* Vk, size_t ld, void* Pp
     using CW = typename Tr<PW>::C;
 #define BI_SU(NF)                                                                                           \
     {                                                                                                       \
-        constexpr int ROWS = su_rows<NF, PW>();                                                             \
-        constexpr size_t SMEM = su_smem_bytes<NF, PW>();                                                    \
+        constexpr int ROWS = su_smem_bytes<NF, PW, P>(128) <= 200000 ? 128 : 64;                            \
+        v_update_kernel<P, NF><<<(unsigned)((n + 255) / 256), 256, 0, st>>>((S2*)Vnext, (const S2*)W, ld, n, ctl, \
+                                                                           (const CW*)coefS, hscale);       \
+        constexpr size_t SMEM = su_smem_bytes<NF, PW, P>(ROWS);                                             \
         static bool attr = false;                                                                           \
         if (!attr) {                                                                                        \
-            cudaFuncSetAttribute(shift_update_kernel<P, PW, NF, ROWS>,                                      \
+            cudaFuncSetAttribute(shift_tile_kernel<P, PW, NF, ROWS>,                                        \
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);                    \
             attr = true;                                                                                    \
         }                                                                                                   \
-        int g = (int)((n + ROWS - 1) / ROWS);                                                               \
-        shift_update_kernel<P, PW, NF, ROWS><<<g, ROWS, SMEM, st>>>(                                        \
-            (S2*)Vnext, (const S2*)W, (const S2*)Vk, ld, (W2*)Pp, (W2*)X, ldw, n, s, m, ctl, (const CW*)coefS, \
-            (const CW*)coefU, (const CW*)coefL, active, hscale);                                            \
+        const unsigned g = (unsigned)(((n + ROWS - 1) / ROWS) * (size_t)s);                                 \
+        shift_tile_kernel<P, PW, NF, ROWS><<<g, ROWS, SMEM, st>>>(                                          \
+            (const S2*)Vnext, (const S2*)Vk, ld, (W2*)Pp, (W2*)X, ldw, n, s, m, ctl, (const CW*)coefU,      \
+            (const CW*)coefL, active, hscale);                                                              \
     }
     BI_DISPATCH_NF(nf_max, BI_SU)
 #undef BI_SU
