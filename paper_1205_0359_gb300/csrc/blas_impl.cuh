@@ -230,16 +230,25 @@ __global__ void __launch_bounds__(256) init_basis_kernel(typename Tr<P>::S2* __r
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     const R scl = (P == PBF16 || P == PF16) ? R(hscale) : R(1);
-    double2 b[NF];
+    // the product is formed in the arithmetic precision of the storage: FP64
+    // for FP64 fields, FP32 otherwise (the result is stored in FP32 or less)
+    using C = typename Tr<P>::C;
+    C b[NF];
 #pragma unroll
-    for (int a = 0; a < NF; ++a) b[a] = a < nf_in ? B[(size_t)a * ldb + e] : make_double2(0.0, 0.0);
+    for (int a = 0; a < NF; ++a) {
+        double2 v = a < nf_in ? B[(size_t)a * ldb + e] : make_double2(0.0, 0.0);
+        b[a] = mk(R(v.x), R(v.y));
+    }
 #pragma unroll
     for (int c = 0; c < NF; ++c) {
         if (c < m1) {
-            double2 acc = make_double2(0.0, 0.0);
+            C acc = mk(R(0), R(0));
 #pragma unroll
-            for (int a = 0; a < NF; ++a) cfma(acc, b[a], ss[a * NF + c]);
-            Elem<P>::st(V1 + (size_t)c * ldv, e, mk(R(acc.x), R(acc.y)), scl);
+            for (int a = 0; a < NF; ++a) {
+                const double2 sv = ss[a * NF + c];
+                cfma(acc, b[a], mk(R(sv.x), R(sv.y)));
+            }
+            Elem<P>::st(V1 + (size_t)c * ldv, e, acc, scl);
         }
     }
 }
