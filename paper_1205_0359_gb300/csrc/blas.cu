@@ -10,6 +10,13 @@ using namespace blas_impl;
 size_t gram_partial_doubles(int nf_max) { return (size_t)ntiles_of(nf_max, 0) * 1024 * GSLOTS; }
 
 int gram_blocks(size_t n, int nf_max) {
+    if (nf_max <= 16) {
+        // tiled kernel: a few CTAs per SM, each walking many row tiles
+        size_t tiles_rows = (n + GR - 1) / GR;
+        size_t nb = 152 * 2;
+        if (nb > tiles_rows) nb = tiles_rows;
+        return (int)(nb < 1 ? 1 : nb);
+    }
     int tiles = ntiles_of(nf_max, 0);
     int nb = (152 * 8 + tiles - 1) / tiles;
     size_t maxb = (n + GT - 1) / GT;
@@ -21,6 +28,17 @@ int gram_blocks(size_t n, int nf_max) {
 
 void launch_gram(int prec, const void* X, const void* Y, size_t ld, size_t n, const Ctl* ctl, int nf_static,
                  int nf_max, int herm, int diag_yy, double* partials, int nblk, float hscale, cudaStream_t st) {
+    if (nf_max <= 16) {
+        // shared-memory tiled kernel: one CTA per partial slot, nblk CTAs
+        Ctl* c = const_cast<Ctl*>(ctl);
+        switch (prec) {
+            case P64: launch_gram_tile_t<P64>(X, Y, ld, n, c, nf_static, nf_max, herm, diag_yy, partials, nblk, hscale, st); break;
+            case P32: launch_gram_tile_t<P32>(X, Y, ld, n, c, nf_static, nf_max, herm, diag_yy, partials, nblk, hscale, st); break;
+            case PBF16: launch_gram_tile_t<PBF16>(X, Y, ld, n, c, nf_static, nf_max, herm, diag_yy, partials, nblk, hscale, st); break;
+            case PF16: launch_gram_tile_t<PF16>(X, Y, ld, n, c, nf_static, nf_max, herm, diag_yy, partials, nblk, hscale, st); break;
+        }
+        return;
+    }
     dim3 grid(ntiles_of(nf_max, herm), nblk);
     switch (prec) {
         case P64: gram_kernel<P64><<<grid, GT, 0, st>>>((const double2*)X, (const double2*)Y, ld, n, ctl, nf_static, nf_max, herm, diag_yy, partials, hscale); break;

@@ -309,6 +309,194 @@ __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bu
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// ---------------------------------------------------------------------------
+// Gram product G = X^H Y (nf x nf, nf <= 16) with row tiles staged in shared
+// memory.  Each CTA walks row tiles of GR rows (tile q, q + gridDim.x, ...)
+// through a ring of GNST staging buffers.  One producer warp fills a buffer
+// with the GR-element run of every field of X (and of Y unless X == Y) by
+// bulk asynchronous copies, completion on the buffer's "full" mbarrier; the
+// consumer warps, one per 4 x 4 tile of the Gram matrix with lanes over rows,
+// accumulate in registers (FP32, FP64 for FP64 fields) and release the buffer
+// on its "empty" mbarrier.  No block-wide barrier inside the loop.  A
+// fixed-order warp reduction at the end writes the CTA's partial sums in the
+// layout the m x m kernels reduce ([tile][CTA][36]).  Every wait is bounded;
+// on timeout the CTA drains its copies, flags the control block (if any) and
+// writes NaN partials.
+constexpr int GR = 128;              // rows per staged tile
+// staging buffers per CTA: 4 (3 for FP64 fields, to stay within shared memory)
+template <int P>
+constexpr int gram_stages() { return P == P64 ? 3 : 4; }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <int P>
+__global__ void __launch_bounds__(544) gram_tile_kernel(const typename Tr<P>::S2* __restrict__ X,
+                                                        const typename Tr<P>::S2* __restrict__ Y, size_t ld,
+                                                        size_t n, Ctl* __restrict__ ctl, int nf_static, int nf_max,
+                                                        int herm, int diag_yy, double* __restrict__ partials,
+                                                        float hscale) {
+    using C = typename Tr<P>::C;
+    using R = typename Tr<P>::R;
+    using SE = typename Tr<P>::S2;
+    constexpr int GNST = gram_stages<P>();
+    int nf = nf_static;
+    if (ctl) {
+        if (ctl->done) return;
+        nf = ctl->mk;
+    }
+    extern __shared__ __align__(128) unsigned char g_smem[];
+    const bool same = (X == Y);
+    const size_t stage = (size_t)(same ? nf_max : 2 * nf_max) * GR;   // elements per staging buffer
+    SE* buf0 = reinterpret_cast<SE*>(g_smem);
+    uint64_t* full = reinterpret_cast<uint64_t*>(g_smem + GNST * stage * sizeof(SE));
+    uint64_t* empty = full + GNST;
+    const int T = (nf_max + 3) / 4;
+    const int ncons = ntiles_of(nf_max, herm);        // consumer warps; warp ncons produces
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const size_t ntr = (n + GR - 1) / GR;
+    const size_t G = gridDim.x;
+
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < GNST; ++b) {
+            mbar_init(&full[b], 1);
+            mbar_init(&empty[b], ncons);
+        }
+        mbar_fence_init();
+    }
+    __syncthreads();
+    bool ok = true;
+    if (warp == ncons) {
+        // producer
+        if (lane == 0) {
+            size_t it = 0;
+            for (size_t q = blockIdx.x; q < ntr; q += G, ++it) {
+                const int b = (int)(it % GNST);
+                if (it >= GNST && !mbar_wait(&empty[b], (uint32_t)((it / GNST - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                const size_t r0 = q * GR;
+                const int rows = (int)((n - r0) < (size_t)GR ? (n - r0) : (size_t)GR);
+                const uint32_t tb = (uint32_t)rows * sizeof(SE);
+                SE* d = buf0 + (size_t)b * stage;
+                mbar_expect_tx(&full[b], (uint32_t)(same ? nf : 2 * nf) * tb);
+                for (int f = 0; f < nf; ++f) {
+                    bulk_g2s(d + (size_t)f * GR, X + (size_t)f * ld + r0, tb, &full[b]);
+                    if (!same) bulk_g2s(d + (size_t)(nf_max + f) * GR, Y + (size_t)f * ld + r0, tb, &full[b]);
+                }
+            }
+            // every issued copy lands before the CTA may exit (the last
+            // GNST fills; earlier ones were waited on through "empty")
+            const size_t first = it > GNST ? it - GNST : 0;
+            for (size_t k = first; k < it; ++k)
+                if (!mbar_wait(&full[k % GNST], (uint32_t)((k / GNST) & 1))) ok = false;
+        }
+    } else {
+        // consumers
+        int ti, tj;
+        tile_coords(warp, T, herm, &ti, &tj);
+        const int i0 = ti * 4, j0 = tj * 4;
+        const int ni = max(0, min(4, nf - i0)), nj = max(0, min(4, nf - j0));
+        const bool dodiag = diag_yy && ti == tj;
+        const R inv = (P == PBF16 || P == PF16) ? R(1) / R(hscale) : R(1);
+        C acc[4][4];
+        R yy[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            yy[a] = R(0);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][c] = mk(R(0), R(0));
+        }
+        size_t it = 0;
+        for (size_t q = blockIdx.x; q < ntr; q += G, ++it) {
+            const int b = (int)(it % GNST);
+            if (!mbar_wait(&full[b], (uint32_t)((it / GNST) & 1))) {
+                ok = false;
+                break;
+            }
+            const int rows = (int)((n - q * GR) < (size_t)GR ? (n - q * GR) : (size_t)GR);
+            const SE* sx = buf0 + (size_t)b * stage;
+            const SE* sy = same ? sx : sx + (size_t)nf_max * GR;
+            if (ni > 0 && nj > 0) {
+                for (int r = lane; r < rows; r += 32) {
+                    C x[4], y[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        x[a] = a < ni ? Elem<P>::ld(sx, (size_t)(i0 + a) * GR + r, inv) : mk(R(0), R(0));
+                        y[a] = a < nj ? Elem<P>::ld(sy, (size_t)(j0 + a) * GR + r, inv) : mk(R(0), R(0));
+                    }
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) cfmac(acc[a][c], x[a], y[c]);
+                    if (dodiag) {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) yy[c] = fma(y[c].x, y[c].x, fma(y[c].y, y[c].y, yy[c]));
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[b]);
+        }
+        // fixed-order warp reduction of the 36 slots, then one write per slot
+        R v[GSLOTS];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                v[2 * (a * 4 + c)] = acc[a][c].x;
+                v[2 * (a * 4 + c) + 1] = acc[a][c].y;
+            }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[32 + c] = yy[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int qq = 0; qq < GSLOTS; ++qq) v[qq] += __shfl_down_sync(0xffffffffu, v[qq], o);
+        if (lane == 0) {
+            const size_t base = ((size_t)warp * G + blockIdx.x) * GSLOTS;
+#pragma unroll
+            for (int qq = 0; qq < GSLOTS; ++qq) {
+                if constexpr (P == P64)
+                    partials[base + qq] = (double)v[qq];
+                else
+                    reinterpret_cast<float*>(partials)[base + qq] = (float)v[qq];
+            }
+        }
+    }
+    if (__syncthreads_or(!ok)) {
+        // a wait gave up: poison every partial of this CTA
+        if (threadIdx.x == 0 && ctl) atomicExch(&ctl->status, ST_WAIT_TIMEOUT);
+        for (int t = threadIdx.x; t < ncons * GSLOTS; t += blockDim.x) {
+            const size_t at = ((size_t)(t / GSLOTS) * G + blockIdx.x) * GSLOTS + t % GSLOTS;
+            if constexpr (P == P64)
+                partials[at] = __longlong_as_double(0x7ff8000000000000LL);
+            else
+                reinterpret_cast<float*>(partials)[at] = __int_as_float(0x7fc00000);
+        }
+    }
+}
+
+template <int P>
+void launch_gram_tile_t(const void* X, const void* Y, size_t ld, size_t n, Ctl* ctl, int nf_static, int nf_max,
+                        int herm, int diag_yy, double* partials, int nblk, float hscale, cudaStream_t st) {
+    using SE = typename Tr<P>::S2;
+    constexpr int GNST = gram_stages<P>();
+    const int npb = ntiles_of(nf_max, herm);
+    const int nbuf_fields = (X == Y) ? nf_max : 2 * nf_max;
+    const size_t smem = GNST * (size_t)nbuf_fields * GR * sizeof(SE) + 2 * GNST * sizeof(uint64_t);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(gram_tile_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(GNST * 2 * 16 * GR * sizeof(SE) + 2 * GNST * sizeof(uint64_t)));
+        attr = true;
+    }
+    gram_tile_kernel<P><<<nblk, (npb + 1) * 32, smem, st>>>((const SE*)X, (const SE*)Y, ld, n, ctl, nf_static, nf_max, herm,
+                                                      diag_yy, partials, hscale);
+}
+
 // V_{k+1} = W S (one thread per row; W and V in the storage precision)
 template <int P, int NF>
 __global__ void __launch_bounds__(256) v_update_kernel(typename Tr<P>::S2* __restrict__ Vn,
