@@ -20,7 +20,9 @@
  *
  * Pointers: "device or host" arguments may point to device memory or to host
  * memory (pageable or pinned); the library detects which and copies host
- * data in and out on the context's stream.  The caller owns every buffer it
+ * data in and out on the context's stream (results bound for pinned host
+ * memory that is mapped into the device address space are written there
+ * directly by the output kernel).  The caller owns every buffer it
  * passes; the library never frees them.  A context owns its workspace and its
  * packed copies of the gauge field.
  *

@@ -115,6 +115,17 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// device address of page-locked host memory mapped into the device address
+// space (nullptr for device, pageable or unmapped memory)
+void* mapped_host_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 dsbcg_status dmalloc(dsbcg_ctx* c, void** p, size_t bytes) {
     if (bytes == 0) bytes = 16;
     cudaError_t e = cudaMalloc(p, bytes);
@@ -602,6 +613,8 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
     double2* bcanon = nullptr;
     if (b_dev) {
         bcanon = (double2*)B;
+    } else if (void* bmap = mapped_host_ptr(B)) {
+        bcanon = (double2*)bmap;   // pinned and mapped: the kernels read it in place
     } else {
         bcanon = w.X64;        // X64 has >= m*ld complex; used as staging before it is zeroed
         CK(cudaMemcpyAsync(bcanon, B, (size_t)m * n * sizeof(double2), cudaMemcpyHostToDevice, c->st));
@@ -730,6 +743,15 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
         {
             Prof p(c, DSBCG_KCLASS_OTHER);
             launch_unpack_fields(P64, xcanon, w.X64, ld, s * m, c->V, 1.f, c->st);
+        }
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(c->st));
+    } else if (void* xmap = mapped_host_ptr(X)) {
+        // pinned host memory mapped into the device address space: the
+        // unpack kernel writes the canonical layout straight into it
+        {
+            Prof p(c, DSBCG_KCLASS_OTHER);
+            launch_unpack_fields(P64, (double2*)xmap, w.X64, ld, s * m, c->V, 1.f, c->st);
         }
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(c->st));
