@@ -49,15 +49,16 @@ void launch_gram(int prec, const void* X, const void* Y, size_t ld, size_t n, co
 }
 
 void launch_gram_reduce(const double* partials, int nblk, int nf_max, int herm, int diag_yy, double2* G,
-                        double* diag, const Ctl* ctl, int nf_static, cudaStream_t st) {
+                        double* diag, const Ctl* ctl, int nf_static, int fp32, cudaStream_t st) {
     (void)nf_static;
-    gram_reduce_kernel<<<ntiles_of(nf_max, herm), 64, 0, st>>>(partials, nblk, nf_max, herm, diag_yy, G, diag, ctl);
+    gram_reduce_kernel<<<ntiles_of(nf_max, herm), 64, 0, st>>>(partials, nblk, nf_max, herm, diag_yy, G, diag, ctl,
+                                                                fp32);
 }
 
 #define EXTERN_P(P)                                                                                      \
     extern template void launch_bu_t<P>(void*, const void*, const void*, const void*, size_t, size_t, const Ctl*, \
                                         int, const void*, const void*, float, cudaStream_t);                 \
-    extern template void launch_ib_t<P>(void*, size_t, const double2*, size_t, size_t, const double2*,        \
+    extern template void launch_ib_t<P>(void*, size_t, const void*, int, size_t, size_t, const double2*,      \
                                         const Ctl*, int, float, cudaStream_t);                               \
     extern template void launch_su_t<P>(void*, const void*, const void*, size_t, void*, void*, size_t, size_t,  \
                                         int, int, Ctl*, int, const void*, const void*, const void*,           \
@@ -81,13 +82,13 @@ void launch_block_update(int prec, void* W, const void* Y, const void* Vk, const
     }
 }
 
-void launch_init_basis(int prec, void* V1, size_t ldv, const double2* B, size_t ldb, size_t n, const double2* S,
-                       const Ctl* ctl, int nf_in, float hscale, cudaStream_t st) {
+void launch_init_basis(int prec, void* V1, size_t ldv, const void* B, int bprec, size_t ldb, size_t n,
+                       const double2* S, const Ctl* ctl, int nf_in, float hscale, cudaStream_t st) {
     switch (prec) {
-        case P64: launch_ib_t<P64>(V1, ldv, B, ldb, n, S, ctl, nf_in, hscale, st); break;
-        case P32: launch_ib_t<P32>(V1, ldv, B, ldb, n, S, ctl, nf_in, hscale, st); break;
-        case PBF16: launch_ib_t<PBF16>(V1, ldv, B, ldb, n, S, ctl, nf_in, hscale, st); break;
-        case PF16: launch_ib_t<PF16>(V1, ldv, B, ldb, n, S, ctl, nf_in, hscale, st); break;
+        case P64: launch_ib_t<P64>(V1, ldv, B, bprec, ldb, n, S, ctl, nf_in, hscale, st); break;
+        case P32: launch_ib_t<P32>(V1, ldv, B, bprec, ldb, n, S, ctl, nf_in, hscale, st); break;
+        case PBF16: launch_ib_t<PBF16>(V1, ldv, B, bprec, ldb, n, S, ctl, nf_in, hscale, st); break;
+        case PF16: launch_ib_t<PF16>(V1, ldv, B, bprec, ldb, n, S, ctl, nf_in, hscale, st); break;
     }
 }
 

@@ -137,10 +137,11 @@ __global__ void __launch_bounds__(GT) gram_kernel(const typename Tr<P>::S2* __re
     }
 }
 
-// G[i][j] (M_MAX x M_MAX) from the per-CTA partials; one CTA per tile
+// G[i][j] (M_MAX x M_MAX) from the per-CTA partials (FP32 words when fp32,
+// as written by the reduced-precision Gram kernels); one CTA per tile
 static __global__ void gram_reduce_kernel(const double* __restrict__ partials, int nblk, int nf_max, int herm,
                                    int diag_yy, double2* __restrict__ G, double* __restrict__ diag,
-                                   const Ctl* __restrict__ ctl) {
+                                   const Ctl* __restrict__ ctl, int fp32) {
     if (ctl && ctl->done) return;
     const int T = (nf_max + 3) / 4;
     const int tile = blockIdx.x;
@@ -148,9 +149,14 @@ static __global__ void gram_reduce_kernel(const double* __restrict__ partials, i
     tile_coords(tile, T, herm, &ti, &tj);
     const int q = threadIdx.x;
     if (q >= GSLOTS) return;
-    const double* p = partials + (size_t)tile * nblk * GSLOTS;
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += p[(size_t)b * GSLOTS + q];
+    if (fp32) {
+        const float* p = reinterpret_cast<const float*>(partials) + (size_t)tile * nblk * GSLOTS;
+        for (int b = 0; b < nblk; ++b) s += (double)p[(size_t)b * GSLOTS + q];
+    } else {
+        const double* p = partials + (size_t)tile * nblk * GSLOTS;
+        for (int b = 0; b < nblk; ++b) s += p[(size_t)b * GSLOTS + q];
+    }
     if (q < 32) {
         int a = (q >> 1) >> 2, bb = (q >> 1) & 3;
         int i = ti * 4 + a, j = tj * 4 + bb;
@@ -217,37 +223,43 @@ __global__ void __launch_bounds__(256) block_update_kernel(typename Tr<P>::S2* _
 }
 
 // V1 = B S: B FP64 (nf_in fields), S FP64 M_MAX x M_MAX, V1 storage precision (ctl->mk fields)
-template <int P, int NF>
+template <int P, int NF, int PIN>
 __global__ void __launch_bounds__(256) init_basis_kernel(typename Tr<P>::S2* __restrict__ V1, size_t ldv,
-                                                         const double2* __restrict__ B, size_t ldb, size_t n,
-                                                         const double2* __restrict__ S,
+                                                         const typename Tr<PIN>::S2* __restrict__ B, size_t ldb,
+                                                         size_t n, const double2* __restrict__ S,
                                                          const Ctl* __restrict__ ctl, int nf_in, float hscale) {
+    // the product is formed in the arithmetic precision of the storage: FP64
+    // for FP64 fields, FP32 otherwise (the result is stored in FP32 or less);
+    // S is converted once per CTA (FP64 -> FP32 conversion runs at the FP64
+    // rate on GB300)
     using R = typename Tr<P>::R;
+    using C = typename Tr<P>::C;
     const int m1 = ctl->mk;
-    __shared__ double2 ss[NF * NF];
-    for (int t = threadIdx.x; t < NF * NF; t += blockDim.x) ss[t] = S[(t / NF) * M_MAX + (t % NF)];
+    __shared__ C ss[NF * NF];
+    for (int t = threadIdx.x; t < NF * NF; t += blockDim.x) {
+        const double2 v = S[(t / NF) * M_MAX + (t % NF)];
+        ss[t] = mk(R(v.x), R(v.y));
+    }
     __syncthreads();
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     const R scl = (P == PBF16 || P == PF16) ? R(hscale) : R(1);
-    // the product is formed in the arithmetic precision of the storage: FP64
-    // for FP64 fields, FP32 otherwise (the result is stored in FP32 or less)
-    using C = typename Tr<P>::C;
     C b[NF];
 #pragma unroll
     for (int a = 0; a < NF; ++a) {
-        double2 v = a < nf_in ? B[(size_t)a * ldb + e] : make_double2(0.0, 0.0);
-        b[a] = mk(R(v.x), R(v.y));
+        if (a < nf_in) {
+            const auto v = B[(size_t)a * ldb + e];
+            b[a] = mk(R(v.x), R(v.y));
+        } else {
+            b[a] = mk(R(0), R(0));
+        }
     }
 #pragma unroll
     for (int c = 0; c < NF; ++c) {
         if (c < m1) {
             C acc = mk(R(0), R(0));
 #pragma unroll
-            for (int a = 0; a < NF; ++a) {
-                const double2 sv = ss[a * NF + c];
-                cfma(acc, b[a], mk(R(sv.x), R(sv.y)));
-            }
+            for (int a = 0; a < NF; ++a) cfma(acc, b[a], ss[a * NF + c]);
             Elem<P>::st(V1 + (size_t)c * ldv, e, acc, scl);
         }
     }
@@ -671,13 +683,22 @@ void launch_bu_t(void* W, const void* Y, const void* Vk, const void* Vp, size_t 
 }
 
 template <int P>
-void launch_ib_t(void* V1, size_t ldv, const double2* B, size_t ldb, size_t n, const double2* S, const Ctl* ctl,
-                 int nf_in, float hscale, cudaStream_t st) {
+void launch_ib_t(void* V1, size_t ldv, const void* B, int bprec, size_t ldb, size_t n, const double2* S,
+                 const Ctl* ctl, int nf_in, float hscale, cudaStream_t st) {
     using S2 = typename Tr<P>::S2;
     int g = (int)((n + 255) / 256);
-#define BI_IB(NF) init_basis_kernel<P, NF><<<g, 256, 0, st>>>((S2*)V1, ldv, B, ldb, n, S, ctl, nf_in, hscale)
-    BI_DISPATCH_NF(nf_in, BI_IB)
+    if (bprec == P64 || P == P64) {
+        // FP64 storage always starts from FP64 right-hand sides
+#define BI_IB(NF) \
+    init_basis_kernel<P, NF, P64><<<g, 256, 0, st>>>((S2*)V1, ldv, (const double2*)B, ldb, n, S, ctl, nf_in, hscale)
+        BI_DISPATCH_NF(nf_in, BI_IB)
 #undef BI_IB
+    } else {
+#define BI_IB(NF) \
+    init_basis_kernel<P, NF, P32><<<g, 256, 0, st>>>((S2*)V1, ldv, (const float2*)B, ldb, n, S, ctl, nf_in, hscale)
+        BI_DISPATCH_NF(nf_in, BI_IB)
+#undef BI_IB
+    }
 }
 
 template <int P>
@@ -712,8 +733,8 @@ void launch_su_t(void* Vnext, const void* W, const void* Vk, size_t ld, void* Pp
 #define BI_INSTANTIATE(P)                                                                                  \
     template void launch_bu_t<P>(void*, const void*, const void*, const void*, size_t, size_t, const Ctl*, int, \
                                  const void*, const void*, float, cudaStream_t);                          \
-    template void launch_ib_t<P>(void*, size_t, const double2*, size_t, size_t, const double2*, const Ctl*, int, \
-                                 float, cudaStream_t);                                                     \
+    template void launch_ib_t<P>(void*, size_t, const void*, int, size_t, size_t, const double2*, const Ctl*, \
+                                 int, float, cudaStream_t);                                                \
     template void launch_su_t<P>(void*, const void*, const void*, size_t, void*, void*, size_t, size_t, int, int, \
                                  Ctl*, int, const void*, const void*, const void*, const int*, float,         \
                                  cudaStream_t);

@@ -29,7 +29,10 @@
 
 namespace dsbcg {
 
-enum Prec { P64 = 0, P32 = 1, PBF16 = 2, PF16 = 3 };
+// PDD: double-float ("FP32 pair") fields for the true-residual loop of the
+// reduced-precision solves (see the dd type below); never a storage
+// precision of the Krylov basis.
+enum Prec { P64 = 0, P32 = 1, PBF16 = 2, PF16 = 3, PDD = 4 };
 
 constexpr int M_MAX = 32;      // largest block width (right-hand sides in a block)
 constexpr int S_MAX = 64;      // largest number of shifts
@@ -58,7 +61,7 @@ template <> struct Tr<PF16> {
 };
 
 __host__ __device__ constexpr int prec_bytes(int p) {
-    return p == P64 ? 16 : (p == P32 ? 8 : 4);     // bytes per complex
+    return (p == P64 || p == PDD) ? 16 : (p == P32 ? 8 : 4);     // bytes per complex
 }
 
 // ---------------------------------------------------------------- complex --
@@ -99,6 +102,80 @@ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2
 __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 // i * a
 template <class C> __device__ __forceinline__ C ctimesi(C a) { return mk(-a.y, a.x); }
+
+// ------------------------------------------------------------ double-float --
+// An unevaluated sum hi + lo of two FP32 numbers with |lo| <= ulp(hi) / 2:
+// 48 significand bits, the FP32 exponent range.  GB300 executes FP64 (and
+// FP64 <-> FP32 conversion) at 1/64 of its FP32 rate, so the loop that needs
+// more than FP32 accuracy (true residuals, solution accumulation) runs in
+// this arithmetic on the FP32 pipes.  Error-free transformations:
+//   two_sum        s + e = a + b exactly (Knuth, TAOCP vol. 2, 4.2.2)
+//   quick_two_sum  the same when |a| >= |b| (Dekker 1971)
+//   two_prod       p + e = a * b exactly, e from one fused multiply-add
+// Addition is Dekker's: relative error about 2^-45 of |a| + |b|; the product
+// drops lo * lo (relative error about 2^-46).  Built without fast-math, so
+// the compiler neither reassociates these sums nor contracts them.
+struct dd {
+    float hi, lo;
+    dd() = default;
+    __host__ __device__ explicit constexpr dd(float h) : hi(h), lo(0.f) {}
+    __host__ __device__ constexpr dd(float h, float l) : hi(h), lo(l) {}
+    // nearest pair to a double (host side: constants such as kappa, sigma)
+    static __host__ __device__ dd from_double(double v) {
+        float h = (float)v;
+        return dd(h, (float)(v - (double)h));
+    }
+};
+struct ddc {
+    dd x, y;
+};
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ dd quick_two_sum(float a, float b) {
+    float s = a + b;
+    return dd(s, b - (s - a));
+}
+__device__ __forceinline__ dd operator+(dd a, dd b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e += a.lo + b.lo;
+    return quick_two_sum(s, e);
+}
+__device__ __forceinline__ dd operator-(dd a) { return dd(-a.hi, -a.lo); }
+__device__ __forceinline__ dd operator-(dd a, dd b) { return a + (-b); }
+__device__ __forceinline__ dd operator*(dd a, dd b) {
+    float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return quick_two_sum(p, e);
+}
+// c + a * b (an overload beside the FP32/FP64 fma, which stay visible)
+using ::fma;
+__device__ __forceinline__ dd fma(dd a, dd b, dd c) {
+    float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    float s, t;
+    two_sum(c.hi, p, s, t);
+    t += c.lo + e;
+    return quick_two_sum(s, t);
+}
+__device__ __forceinline__ ddc mk(dd a, dd b) { return ddc{a, b}; }
+// scaling by a power of two (here always a sign): exact on both words
+__device__ __forceinline__ ddc cscale(ddc a, dd s) {
+    return ddc{dd(a.x.hi * s.hi, a.x.lo * s.hi), dd(a.y.hi * s.hi, a.y.lo * s.hi)};
+}
+
+template <> struct Tr<PDD> {
+    using S2 = float2;             // one word plane of a complex element
+    using R = dd;
+    using C = ddc;
+};
 
 // ------------------------------------------------------- element load/store --
 // Flat complex element i of a field (internal order), converted to the

@@ -31,7 +31,7 @@ struct SpinorIO;
 
 template <>
 struct SpinorIO<P64> {
-    static __device__ __forceinline__ void load(const double2* f, size_t V, size_t x, double2 p[12], double) {
+    static __device__ __forceinline__ void load(const double2* f, size_t V, size_t x, double2 p[12], double, size_t) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
             const double2* q = f + ((size_t)c * V + x) * 2;
@@ -39,7 +39,7 @@ struct SpinorIO<P64> {
             p[2 * c + 1] = __ldg(q + 1);
         }
     }
-    static __device__ __forceinline__ void store(double2* f, size_t V, size_t x, const double2 p[12], double) {
+    static __device__ __forceinline__ void store(double2* f, size_t V, size_t x, const double2 p[12], double, size_t) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
             double2* q = f + ((size_t)c * V + x) * 2;
@@ -51,7 +51,7 @@ struct SpinorIO<P64> {
 
 template <>
 struct SpinorIO<P32> {
-    static __device__ __forceinline__ void load(const float2* f, size_t V, size_t x, float2 p[12], float) {
+    static __device__ __forceinline__ void load(const float2* f, size_t V, size_t x, float2 p[12], float, size_t) {
         const float4* q = reinterpret_cast<const float4*>(f);
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
@@ -60,7 +60,7 @@ struct SpinorIO<P32> {
             p[2 * c + 1] = make_float2(v.z, v.w);
         }
     }
-    static __device__ __forceinline__ void store(float2* f, size_t V, size_t x, const float2 p[12], float) {
+    static __device__ __forceinline__ void store(float2* f, size_t V, size_t x, const float2 p[12], float, size_t) {
         float4* q = reinterpret_cast<float4*>(f);
 #pragma unroll
         for (int c = 0; c < 6; ++c)
@@ -70,7 +70,7 @@ struct SpinorIO<P32> {
 
 template <class H2, class Cvt>
 struct Spinor16 {
-    static __device__ __forceinline__ void load(const H2* f, size_t V, size_t x, float2 p[12], float inv) {
+    static __device__ __forceinline__ void load(const H2* f, size_t V, size_t x, float2 p[12], float inv, size_t) {
         const uint2* q = reinterpret_cast<const uint2*>(f);
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
@@ -83,7 +83,7 @@ struct Spinor16 {
             }
         }
     }
-    static __device__ __forceinline__ void store(H2* f, size_t V, size_t x, const float2 p[12], float sc) {
+    static __device__ __forceinline__ void store(H2* f, size_t V, size_t x, const float2 p[12], float sc, size_t) {
         uint2* q = reinterpret_cast<uint2*>(f);
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
@@ -106,11 +106,40 @@ struct CvtH {
 };
 template <> struct SpinorIO<PBF16> : Spinor16<__nv_bfloat162, CvtBF> {};
 template <> struct SpinorIO<PF16> : Spinor16<__half2, CvtH> {};
+// double-float fields: an FP32 hi plane and, plo float2 further on, an FP32
+// lo plane, each in the pair-chunk layout
+template <>
+struct SpinorIO<PDD> {
+    static __device__ __forceinline__ void load(const float2* f, size_t V, size_t x, ddc p[12], dd, size_t plo) {
+        const float4* qh = reinterpret_cast<const float4*>(f);
+        const float4* ql = reinterpret_cast<const float4*>(f + plo);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            float4 h = __ldg(qh + (size_t)c * V + x);
+            float4 l = __ldg(ql + (size_t)c * V + x);
+            p[2 * c] = ddc{dd(h.x, l.x), dd(h.y, l.y)};
+            p[2 * c + 1] = ddc{dd(h.z, l.z), dd(h.w, l.w)};
+        }
+    }
+    static __device__ __forceinline__ void store(float2* f, size_t V, size_t x, const ddc p[12], dd, size_t plo) {
+        float4* qh = reinterpret_cast<float4*>(f);
+        float4* ql = reinterpret_cast<float4*>(f + plo);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            qh[(size_t)c * V + x] = make_float4(p[2 * c].x.hi, p[2 * c].y.hi, p[2 * c + 1].x.hi, p[2 * c + 1].y.hi);
+            ql[(size_t)c * V + x] = make_float4(p[2 * c].x.lo, p[2 * c].y.lo, p[2 * c + 1].x.lo, p[2 * c + 1].y.lo);
+        }
+    }
+};
 
+// link entry at p; a double-float link keeps its lo plane loff float2 further on
 template <int P>
-__device__ __forceinline__ typename Tr<P>::C ld_link(const typename Tr<P>::S2* p) {
+__device__ __forceinline__ typename Tr<P>::C ld_link(const typename Tr<P>::S2* p, size_t loff) {
     if constexpr (P == P64 || P == P32) {
         return __ldg(p);
+    } else if constexpr (P == PDD) {
+        float2 h = __ldg(p), l = __ldg(p + loff);
+        return ddc{dd(h.x, l.x), dd(h.y, l.y)};
     } else if constexpr (P == PBF16) {
         return __bfloat1622float2(*p);
     } else {
@@ -161,8 +190,8 @@ __device__ __forceinline__ int neighbour(const Geom& g, int x, const Site& s, in
 // Uh = U h (fwd) or U^H h (bwd) for the 2 x 3 half spinor h; entry e of the
 // link is at u[e * stride] (global memory, read-only path)
 template <int P, class C>
-__device__ __forceinline__ void su3_mul(const typename Tr<P>::S2* __restrict__ u, size_t stride, const C h[2][3],
-                                        C out[2][3], bool adj) {
+__device__ __forceinline__ void su3_mul(const typename Tr<P>::S2* __restrict__ u, size_t stride, size_t loff,
+                                        const C h[2][3], C out[2][3], bool adj) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
 #pragma unroll
@@ -173,11 +202,11 @@ __device__ __forceinline__ void su3_mul(const typename Tr<P>::S2* __restrict__ u
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
             if (!adj) {
-                C uab = ld_link<P>(u + (a * 3 + b) * stride);
+                C uab = ld_link<P>(u + (a * 3 + b) * stride, loff);
 #pragma unroll
                 for (int sp = 0; sp < 2; ++sp) cfma(out[sp][a], uab, h[sp][b]);
             } else {
-                C uba = ld_link<P>(u + (b * 3 + a) * stride);     // (U^H)_ab = conj(U_ba)
+                C uba = ld_link<P>(u + (b * 3 + a) * stride, loff);     // (U^H)_ab = conj(U_ba)
 #pragma unroll
                 for (int sp = 0; sp < 2; ++sp) cfmac(out[sp][a], uba, h[sp][b]);
             }
@@ -186,7 +215,7 @@ __device__ __forceinline__ void su3_mul(const typename Tr<P>::S2* __restrict__ u
 }
 
 template <int P>
-__global__ void __launch_bounds__(32, 16) dslash_kernel(typename Tr<P>::S2* __restrict__ out,
+__global__ void __launch_bounds__(32, P == PDD ? 8 : 16) dslash_kernel(typename Tr<P>::S2* __restrict__ out,
                                                    const typename Tr<P>::S2* __restrict__ in,
                                                    size_t ld, const typename Tr<P>::S2* __restrict__ links,
                                                    Geom g, typename Tr<P>::R kappa, int g5in, int g5out,
@@ -207,8 +236,15 @@ __global__ void __launch_bounds__(32, 16) dslash_kernel(typename Tr<P>::S2* __re
     const size_t V = (size_t)g.V;
     const int x = site0 + tx;
     if (x >= g.V) return;
-    const R inv = (P == PBF16 || P == PF16) ? R(1) / R(hscale) : R(1);
-    const R scl = (P == PBF16 || P == PF16) ? R(hscale) : R(1);
+    R inv = R(1), scl = R(1);
+    if constexpr (P == PBF16 || P == PF16) {
+        inv = R(1) / R(hscale);
+        scl = R(hscale);
+    }
+    // double-float fields: lo plane half a field stride after the hi plane;
+    // double-float links: lo plane 36 V entries after the hi plane
+    const size_t plo = (P == PDD) ? ld / 2 : 0;
+    const size_t loff = (P == PDD) ? 36 * (size_t)g.V : 0;
     const Site s = coords(g, x);
     const R g5i = g5in ? R(-1) : R(1);
 
@@ -227,7 +263,7 @@ __global__ void __launch_bounds__(32, 16) dslash_kernel(typename Tr<P>::S2* __re
                 float sgn;
                 int y = neighbour(g, x, s, mu, dir == 0 ? 1 : -1, &sgn);
                 C p[12];
-                SpinorIO<P>::load(fin, V, (size_t)y, p, inv);
+                SpinorIO<P>::load(fin, V, (size_t)y, p, inv, plo);
                 const R sg = R(sgn);
                 const R su = sg * g5i;          // gamma_5 on input flips the upper spins
                 const R sl_ = sg;
@@ -250,7 +286,7 @@ __global__ void __launch_bounds__(32, 16) dslash_kernel(typename Tr<P>::S2* __re
                 }
                 C uh[2][3];
                 // forward hop: U_mu(x); backward hop: U_mu(x - mu) = U_mu(y)
-                su3_mul<P>(links + (size_t)mu * 9 * V + (dir == 0 ? x : y), V, h, uh, dir != 0);
+                su3_mul<P>(links + (size_t)mu * 9 * V + (dir == 0 ? x : y), V, loff, h, uh, dir != 0);
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     acc[0][a] = cadd(acc[0][a], uh[0][a]);
@@ -271,7 +307,7 @@ __global__ void __launch_bounds__(32, 16) dslash_kernel(typename Tr<P>::S2* __re
             }
         }
         C p[12];
-        SpinorIO<P>::load(fin, V, (size_t)x, p, inv);
+        SpinorIO<P>::load(fin, V, (size_t)x, p, inv, plo);
         const R go = g5out ? R(-1) : R(1);
 #pragma unroll
         for (int sp = 0; sp < 4; ++sp) {
@@ -285,7 +321,7 @@ __global__ void __launch_bounds__(32, 16) dslash_kernel(typename Tr<P>::S2* __re
                 p[sp * 3 + a] = cscale(v, sgo);
             }
         }
-        SpinorIO<P>::store(out + (size_t)f * ld, V, (size_t)x, p, scl);
+        SpinorIO<P>::store(out + (size_t)f * ld, V, (size_t)x, p, scl, plo);
     }
 }
 
@@ -321,6 +357,12 @@ void launch_dslash(int prec, void* out, const void* in, size_t ld, const void* l
             dslash_kernel<PF16><<<grid, block, sm, st>>>((__half2*)out, (const __half2*)in, ld,
                                                           (const __half2*)links, g, (float)kappa, g5in,
                                                           g5out, ctl, nf_static, hscale, nf_grid);
+            break;
+        case PDD:
+            // ld: field stride in float2 words (two planes of the complex stride)
+            dslash_kernel<PDD><<<grid, block, sm, st>>>((float2*)out, (const float2*)in, ld,
+                                                         (const float2*)links, g, dd::from_double(kappa), g5in,
+                                                         g5out, ctl, nf_static, hscale, nf_grid);
             break;
     }
 }

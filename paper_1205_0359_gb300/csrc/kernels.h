@@ -25,6 +25,13 @@ void launch_unpack_fields(int prec, double2* dst, const void* src, size_t ld, in
                           float hscale, cudaStream_t st);
 // canonical complex128 [site][4][3][3] -> internal links [mu][9][site]
 void launch_pack_links(int prec, void* dst, const double2* src, size_t V, cudaStream_t st);
+// double-float fields (field f: FP32 hi plane at f * 2 ld, lo plane at
+// f * 2 ld + ld, float2 words; internal order)
+void launch_pack_pairs(float2* dst, size_t ld, const double2* src, int m, size_t V, cudaStream_t st);
+void launch_unpack_pairs(double2* dst, const float2* src, size_t ld, int m, size_t V, cudaStream_t st);
+void launch_accumulate_pairs(float2* y, size_t ld, const float2* x, size_t ldx, int m, size_t n, cudaStream_t st);
+void launch_residual_pairs(float2* r, const float2* b, const float2* x, const float2* ax, size_t ld, int m,
+                           size_t n, double sigma, double* partials, int nblk, cudaStream_t st);
 // counts NaN/Inf entries of a complex128 array into *flag (device int)
 void launch_check_finite(const double2* p, size_t count, int* flag, cudaStream_t st);
 // y_f += x_f (FP64 += work precision), fields listed by index arrays on the host
@@ -54,14 +61,15 @@ void launch_gram(int prec, const void* X, const void* Y, size_t ld, size_t n, co
 size_t gram_partial_doubles(int nf_max);
 // reduce partials -> G (FP64, M_MAX x M_MAX, complex), diag (M_MAX)
 void launch_gram_reduce(const double* partials, int nblk, int nf_max, int herm, int diag_yy,
-                        double2* G, double* diag, const Ctl* ctl, int nf_static,
+                        double2* G, double* diag, const Ctl* ctl, int nf_static, int fp32,
                         cudaStream_t st);
 // W = Y - V a - Vp b^H, coefficients from the device (work precision copies)
 void launch_block_update(int prec, void* W, const void* Y, const void* Vk, const void* Vp,
                          size_t ld, size_t n, const Ctl* ctl, int nf_max,
                          const void* coef_a, const void* coef_bh, float hscale, cudaStream_t st);
-// V1 = B S (FP64 B, storage-precision V1), S from device (FP64, M_MAX x M_MAX)
-void launch_init_basis(int prec, void* V1, size_t ldv, const double2* B, size_t ldb, size_t n,
+// V1 = B S (B in precision bprec: FP64, or FP32 for reduced storage;
+// storage-precision V1), S from device (FP64, M_MAX x M_MAX)
+void launch_init_basis(int prec, void* V1, size_t ldv, const void* B, int bprec, size_t ldb, size_t n,
                        const double2* S, const Ctl* ctl, int nf_in, float hscale, cudaStream_t st);
 // fused shift update (kernel (d)): V_{k+1} = W S; for active shifts
 // X_j += P_j Ut_j and P_j <- V_{k+1} - P_j LhT_j.  P and X hold s blocks of

@@ -83,7 +83,99 @@ __global__ void accumulate_kernel(double2* __restrict__ y, size_t ldy, const typ
     }
 }
 
+// ---- double-float fields: field f has an FP32 hi plane at f * 2 ld and an
+// FP32 lo plane at f * 2 ld + ld (float2 words), both in the internal order
+
+__global__ void pack_pairs_kernel(float2* __restrict__ dst, size_t ld, const double2* __restrict__ src, int m,
+                                  size_t V) {
+    const size_t n = 12 * V;
+    const size_t total = (size_t)m * n;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        size_t f = t / n, i = t % n;
+        size_t x = i / 12;
+        int c = (int)(i % 12);
+        double2 v = src[t];
+        const float hx = __double2float_rn(v.x), hy = __double2float_rn(v.y);
+        const size_t at = f * 2 * ld + fidx<P32>(V, x, c);
+        dst[at] = make_float2(hx, hy);
+        dst[at + ld] = make_float2(__double2float_rn(v.x - (double)hx), __double2float_rn(v.y - (double)hy));
+    }
+}
+
+__global__ void unpack_pairs_kernel(double2* __restrict__ dst, const float2* __restrict__ src, size_t ld, int m,
+                                    size_t V) {
+    const size_t n = 12 * V;
+    const size_t total = (size_t)m * n;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        size_t f = t / n, i = t % n;
+        size_t x = i / 12;
+        int c = (int)(i % 12);
+        const size_t at = f * 2 * ld + fidx<P32>(V, x, c);
+        float2 h = src[at], l = src[at + ld];
+        dst[t] = make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
+    }
+}
+
+__global__ void pack_links_pairs_kernel(float2* __restrict__ dst, const double2* __restrict__ src, size_t V) {
+    const size_t total = V * 36;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        size_t x = t / 36;
+        int r = (int)(t % 36);
+        double2 v = src[t];
+        const float hx = __double2float_rn(v.x), hy = __double2float_rn(v.y);
+        const size_t at = (size_t)r * V + x;          // r = mu * 9 + entry
+        dst[at] = make_float2(hx, hy);
+        dst[at + total] = make_float2(__double2float_rn(v.x - (double)hx), __double2float_rn(v.y - (double)hy));
+    }
+}
+
+// y (double-float) += x (FP32 plane), m fields of n complex values
+__global__ void accumulate_pairs_kernel(float2* __restrict__ y, size_t ld, const float2* __restrict__ x, size_t ldx,
+                                        int m, size_t n) {
+    const size_t total = (size_t)m * n;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        size_t f = t / n, i = t % n;
+        const size_t at = f * 2 * ld + i;
+        float2 h = y[at], l = y[at + ld], v = x[f * ldx + i];
+        dd a = dd(h.x, l.x) + dd(v.x), b = dd(h.y, l.y) + dd(v.y);
+        y[at] = make_float2(a.hi, b.hi);
+        y[at + ld] = make_float2(a.lo, b.lo);
+    }
+}
+
 constexpr int RES_THREADS = 256;
+
+// r = b - sigma x - ax for double-float fields (grid (nblk, m)); squared
+// column norms from the hi words, summed in FP32 per CTA
+__global__ void residual_pairs_kernel(float2* __restrict__ r, const float2* __restrict__ b,
+                                      const float2* __restrict__ x, const float2* __restrict__ ax, size_t ld,
+                                      size_t n, dd sigma, double* __restrict__ partials, int nblk) {
+    const int f = blockIdx.y;
+    const size_t off = (size_t)f * 2 * ld;
+    float acc = 0.f;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)nblk * blockDim.x) {
+        const size_t h = off + i, l = off + ld + i;
+        float2 bh = b[h], bl = b[l], xh = x[h], xl = x[l], ah = ax[h], al = ax[l];
+        dd rx = dd(bh.x, bl.x) - sigma * dd(xh.x, xl.x) - dd(ah.x, al.x);
+        dd ry = dd(bh.y, bl.y) - sigma * dd(xh.y, xl.y) - dd(ah.y, al.y);
+        r[h] = make_float2(rx.hi, ry.hi);
+        r[l] = make_float2(rx.lo, ry.lo);
+        acc = fmaf(rx.hi, rx.hi, fmaf(ry.hi, ry.hi, acc));
+    }
+    __shared__ float red[RES_THREADS / 32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float v = threadIdx.x < RES_THREADS / 32 ? red[threadIdx.x] : 0.f;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) partials[(size_t)f * nblk + blockIdx.x] = (double)v;
+    }
+}
 
 // one block column per field: grid (nblk, m)
 __global__ void residual_kernel(double2* __restrict__ r, const double2* __restrict__ b,
@@ -156,9 +248,28 @@ void launch_unpack_fields(int prec, double2* dst, const void* src, size_t ld, in
     }
 }
 
+void launch_pack_pairs(float2* dst, size_t ld, const double2* src, int m, size_t V, cudaStream_t st) {
+    pack_pairs_kernel<<<grid_for((size_t)m * 12 * V), 256, 0, st>>>(dst, ld, src, m, V);
+}
+
+void launch_unpack_pairs(double2* dst, const float2* src, size_t ld, int m, size_t V, cudaStream_t st) {
+    unpack_pairs_kernel<<<grid_for((size_t)m * 12 * V), 256, 0, st>>>(dst, src, ld, m, V);
+}
+
+void launch_accumulate_pairs(float2* y, size_t ld, const float2* x, size_t ldx, int m, size_t n, cudaStream_t st) {
+    accumulate_pairs_kernel<<<grid_for((size_t)m * n), 256, 0, st>>>(y, ld, x, ldx, m, n);
+}
+
+void launch_residual_pairs(float2* r, const float2* b, const float2* x, const float2* ax, size_t ld, int m,
+                           size_t n, double sigma, double* partials, int nblk, cudaStream_t st) {
+    dim3 grid(nblk, m);
+    residual_pairs_kernel<<<grid, RES_THREADS, 0, st>>>(r, b, x, ax, ld, n, dd::from_double(sigma), partials, nblk);
+}
+
 void launch_pack_links(int prec, void* dst, const double2* src, size_t V, cudaStream_t st) {
     int g = grid_for(V * 36);
     switch (prec) {
+        case PDD: pack_links_pairs_kernel<<<g, 256, 0, st>>>((float2*)dst, src, V); break;
         case P64: pack_links_kernel<P64><<<g, 256, 0, st>>>((double2*)dst, src, V); break;
         case P32: pack_links_kernel<P32><<<g, 256, 0, st>>>((float2*)dst, src, V); break;
         case PBF16: pack_links_kernel<PBF16><<<g, 256, 0, st>>>((__nv_bfloat162*)dst, src, V); break;

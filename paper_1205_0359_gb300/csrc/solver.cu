@@ -1,7 +1,7 @@
 // Host orchestration and the C ABI (include/dsbcg.h).
 //
 // A solve (Sec. 3) runs as:
-//   1. pack B into the internal FP64 layout; ||b_i||;
+//   1. pack B into the internal high-precision layout; ||b_i||;
 //   2. joint inner solve: the block Lanczos process of A seeded with B, and
 //      every shift's block root-free Cholesky recurrences, in the storage
 //      precision (FP32 arithmetic for FP32/BF16/FP16 storage, FP64 for FP64);
@@ -9,15 +9,19 @@
 //      widths and the convergence state from a device-resident control block,
 //      so the host enqueues steps without synchronising and only polls the
 //      `done` flag every `poll_every` steps;
-//   3. FP64 true residuals r_ij = b_i - (sigma_j + A) x_ij (reliable update);
+//   3. true residuals r_ij = b_i - (sigma_j + A) x_ij (reliable update) in
+//      high precision: FP64 for FP64 storage, double-float (pairs of FP32
+//      words, 48-bit significands, FP32 pipes) for the reduced storages,
+//      because GB300 runs FP64 arithmetic at 1/64 of the FP32 rate;
 //   4. every shift with a residual above tol is restarted on its own true
 //      residual (block CG on sigma_j I + A, same kernels with s = 1) and its
-//      FP64 solution corrected, until every ||r_ij|| <= tol ||b_i|| or the
-//      restart cap is reached.
+//      high-precision solution corrected, until every ||r_ij|| <= tol ||b_i||
+//      or the restart cap is reached.
 // The paper's own code runs in FP64 only (Sec. 4); the reduced-precision
-// inner iteration with FP64 true-residual restarts is a GB300-specific
-// addition.  Restarting is valid because the Galerkin iterate of a restarted
-// process is again of the form of Eq. 3.2 for the new right-hand side.
+// inner iteration with high-precision true-residual restarts is a
+// GB300-specific addition.  Restarting is valid because the Galerkin iterate
+// of a restarted process is again of the form of Eq. 3.2 for the new
+// right-hand side.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -53,7 +57,7 @@ struct dsbcg_ctx {
     double kappa = 0;
     cudaStream_t st = nullptr;
     double2* gauge64 = nullptr;          // canonical copy of the links (device)
-    void* links[4] = {nullptr, nullptr, nullptr, nullptr};
+    void* links[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // per Prec (PDD: double-float)
     float hscale = 1.f;
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -255,30 +259,41 @@ void prof_collect(dsbcg_ctx* c) {
     c->ev_live.clear();
 }
 
-// ---- FP64 operator on internal FP64 fields ----------------------------------
-// out = A in for nf FP64 fields (tmp receives D in)
-void apply_A64(dsbcg_ctx* c, double2* out, const double2* in, double2* tmp, int nf) {
+// ---- high-precision operator and true residual ------------------------------
+// The true-residual loop runs on "high-precision" fields hp: FP64 (P64) for
+// FP64 storage, double-float (PDD) for the reduced storages.  Both take 16
+// bytes per complex, so buffers and byte offsets are the same; a PDD field
+// is an FP32 hi plane and an FP32 lo plane of ld complex each.
+inline size_t hp_ld(const dsbcg_ctx* c, int hp) { return hp == PDD ? 2 * c->ld : c->ld; }
+
+// out = A in for nf high-precision fields (tmp receives D in)
+void apply_Ahp(dsbcg_ctx* c, int hp, void* out, const void* in, void* tmp, int nf) {
     {
         Prof p(c, DSBCG_KCLASS_RESIDUAL);
-        launch_dslash(P64, tmp, in, c->ld, c->links[P64], c->g, c->kappa, 0, 0, nullptr, nf, nf, 1.f, c->st);
+        launch_dslash(hp, tmp, in, hp_ld(c, hp), c->links[hp], c->g, c->kappa, 0, 0, nullptr, nf, nf, 1.f, c->st);
     }
     {
         Prof p(c, DSBCG_KCLASS_RESIDUAL);
-        launch_dslash(P64, out, tmp, c->ld, c->links[P64], c->g, c->kappa, 1, 1, nullptr, nf, nf, 1.f, c->st);
+        launch_dslash(hp, out, tmp, hp_ld(c, hp), c->links[hp], c->g, c->kappa, 1, 1, nullptr, nf, nf, 1.f, c->st);
     }
 }
 
-// r = b - sigma x - A x for m FP64 fields; squared column norms into h_out (host)
-dsbcg_status true_residual(dsbcg_ctx* c, double2* r, const double2* b, const double2* x, int m, double sigma,
-                           double* h_out) {
+// r = b - sigma x - A x for m high-precision fields; squared column norms
+// into h_out (host)
+dsbcg_status true_residual(dsbcg_ctx* c, int hp, double2* r, const double2* b, const double2* x, int m,
+                           double sigma, double* h_out) {
     auto& w = c->ws;
-    apply_A64(c, w.T64b, x, w.T64a, m);
+    apply_Ahp(c, hp, w.T64b, x, w.T64a, m);
     {
         Prof p(c, DSBCG_KCLASS_RESIDUAL, 2);
-        launch_residual(r, b, x, w.T64b, c->ld, m, c->n, sigma, w.rpart, w.rblk, c->st);
+        if (hp == PDD)
+            launch_residual_pairs((float2*)r, (const float2*)b, (const float2*)x, (const float2*)w.T64b, c->ld, m,
+                                  c->n, sigma, w.rpart, w.rblk, c->st);
+        else
+            launch_residual(r, b, x, w.T64b, c->ld, m, c->n, sigma, w.rpart, w.rblk, c->st);
         launch_reduce_cols(w.rpart, w.rblk, m, w.norms, c->st);
     }
-    // two FP64 stencils (m fields in and out, links once each) + b, x, Ax in, r out
+    // two stencils (m fields in and out, links once each) + b, x, Ax in, r out
     c->kbytes[DSBCG_KCLASS_RESIDUAL] +=
         (8.0 * m * c->n + 2.0 * 36 * c->V) * sizeof(double2);
     CK(cudaMemcpyAsync(w.h_norms, w.norms, m * sizeof(double), cudaMemcpyDeviceToHost, c->st));
@@ -296,10 +311,13 @@ struct InnerResult {
     bool converged = false;
 };
 
-// Joint inner solve on the FP64 right-hand sides `rhs` (m_in fields, internal
-// layout): for the shifts sig[0..s_in), X_in[j] (work precision) receives the
-// iterate, targets are absolute residual norms per (j, i).
-dsbcg_status inner_solve(dsbcg_ctx* c, const double2* rhs, int m_in, const double* sig, int s_in,
+// Joint inner solve on the right-hand sides `rhs` (m_in fields of precision
+// rhs_prec, field stride rhs_ld, internal layout: FP64 for FP64 storage, the
+// FP32 hi planes of double-float fields otherwise): for the shifts
+// sig[0..s_in), X_in[j] (work precision) receives the iterate, targets are
+// absolute residual norms per (j, i).
+dsbcg_status inner_solve(dsbcg_ctx* c, const void* rhs, int rhs_prec, size_t rhs_ld, int m_in, const double* sig,
+                         int s_in,
                          const double* targets, int prec, double dtol, int max_steps, int freeze, int poll_every,
                          InnerResult* out, int step_offset, int* conv_step_host) {
     auto& w = c->ws;
@@ -311,24 +329,25 @@ dsbcg_status inner_solve(dsbcg_ctx* c, const double2* rhs, int m_in, const doubl
     CK(cudaMemcpyAsync(w.target, targets, (size_t)s_in * m_in * sizeof(double), cudaMemcpyHostToDevice, c->st));
     CK(cudaMemsetAsync(w.conv_step, 0xff, (size_t)s_in * m_in * sizeof(int), c->st));
     CK(cudaMemsetAsync(w.Xin, 0, (size_t)s_in * m_in * wb, c->st));
-    // a0: G0 = B^H B (FP64), pivoted Cholesky with deflation, V_1 = B S0
+    // a0: G0 = B^H B (in the right-hand sides' precision), pivoted Cholesky
+    // with deflation, V_1 = B S0
     {
         Prof p(c, DSBCG_KCLASS_GRAM);
-        launch_gram(P64, rhs, rhs, ld, n, nullptr, m_in, m_in, 1, 1, w.partials, w.nblk, 1.f, c->st);
+        launch_gram(rhs_prec, rhs, rhs, rhs_ld, n, nullptr, m_in, m_in, 1, 1, w.partials, w.nblk, 1.f, c->st);
     }
     {
         Prof p(c, DSBCG_KCLASS_SMALL, 2);
-        launch_gram_reduce(w.partials, w.nblk, m_in, 1, 1, w.G, w.diag, nullptr, m_in, c->st);
+        launch_gram_reduce(w.partials, w.nblk, m_in, 1, 1, w.G, w.diag, nullptr, m_in, rhs_prec != P64, c->st);
         launch_small_init(w.ss, w.ctl, w.G, w.diag, m_in, s_in, dtol, c->st);
     }
     char* ring = (char*)w.vring;
     {
         Prof p(c, DSBCG_KCLASS_OTHER);
-        launch_init_basis(prec, ring + 1 * (size_t)m_in * fb, ld, rhs, ld, n, small_state_S(w.ss), w.ctl, m_in,
-                          c->hscale, c->st);
+        launch_init_basis(prec, ring + 1 * (size_t)m_in * fb, ld, rhs, rhs_prec, rhs_ld, n, small_state_S(w.ss),
+                          w.ctl, m_in, c->hscale, c->st);
     }
-    c->kbytes[DSBCG_KCLASS_GRAM] += (double)m_in * n * sizeof(double2);
-    c->kbytes[DSBCG_KCLASS_OTHER] += (double)m_in * n * (sizeof(double2) + prec_elem_bytes(prec));
+    c->kbytes[DSBCG_KCLASS_GRAM] += (double)m_in * n * prec_elem_bytes(rhs_prec);
+    c->kbytes[DSBCG_KCLASS_OTHER] += (double)m_in * n * (prec_elem_bytes(rhs_prec) + prec_elem_bytes(prec));
     CK(cudaGetLastError());
     // block steps
     int step = 0;
@@ -497,7 +516,7 @@ dsbcg_status dsbcg_update_gauge(dsbcg_ctx* c, const void* gauge) {
     CK(cudaStreamSynchronize(c->st));
     cudaFree(flag);
     if (h) return DSBCG_ERR_NONFINITE;
-    for (int p = 0; p < 4; ++p) {
+    for (int p = 0; p < 5; ++p) {
         if (c->links[p]) {
             cudaFree(c->links[p]);
             c->links[p] = nullptr;
@@ -510,7 +529,7 @@ dsbcg_status dsbcg_update_gauge(dsbcg_ctx* c, const void* gauge) {
 void dsbcg_destroy(dsbcg_ctx* c) {
     if (!c) return;
     free_ws(c);
-    for (int p = 0; p < 4; ++p)
+    for (int p = 0; p < 5; ++p)
         if (c->links[p]) cudaFree(c->links[p]);
     if (c->gauge64) cudaFree(c->gauge64);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
@@ -596,8 +615,13 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
     if (prec < 0 || prec > 3) return DSBCG_ERR_ARG;
     if (prm.poll_every < 1) prm.poll_every = 1;
     const double dtol = prm.dtol > 0 ? prm.dtol : default_dtol(prec);
+    const bool mixed = prec != P64;
+    // true residuals, B and the accumulated solutions: FP64 fields for FP64
+    // storage, double-float fields (FP32 arithmetic, 48-bit significands)
+    // for the reduced storages
+    const int hp = mixed ? PDD : P64;
     CKS(ensure_links(c, prec));
-    CKS(ensure_links(c, P64));
+    CKS(ensure_links(c, hp));
     CKS(ensure_ws(c, m, s, prec));
     auto& w = c->ws;
     const size_t n = c->n, ld = c->ld;
@@ -608,7 +632,7 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
         c->kbytes[q] = 0;
     }
 
-    // --- inputs: B -> internal FP64 (staging through X64's storage if on the host)
+    // --- inputs: B -> internal high-precision fields (staging through X64's storage if on the host)
     const bool b_dev = is_device_ptr(B), x_dev = is_device_ptr(X);
     double2* bcanon = nullptr;
     if (b_dev) {
@@ -623,7 +647,10 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
     {
         Prof p(c, DSBCG_KCLASS_OTHER, 2);
         launch_check_finite(bcanon, (size_t)m * n, w.flag, c->st);
-        launch_pack_fields(P64, w.B64, ld, bcanon, m, c->V, 1.f, c->st);
+        if (hp == PDD)
+            launch_pack_pairs((float2*)w.B64, ld, bcanon, m, c->V, c->st);
+        else
+            launch_pack_fields(P64, w.B64, ld, bcanon, m, c->V, 1.f, c->st);
     }
     int hflag = 0;
     CK(cudaMemcpyAsync(&hflag, w.flag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
@@ -633,7 +660,11 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
     {
         {
             Prof p(c, DSBCG_KCLASS_OTHER, 2);
-            launch_residual(w.R64, w.B64, w.X64, w.X64, ld, m, n, 0.0, w.rpart, w.rblk, c->st);
+            if (hp == PDD)
+                launch_residual_pairs((float2*)w.R64, (const float2*)w.B64, (const float2*)w.X64,
+                                      (const float2*)w.X64, ld, m, n, 0.0, w.rpart, w.rblk, c->st);
+            else
+                launch_residual(w.R64, w.B64, w.X64, w.X64, ld, m, n, 0.0, w.rpart, w.rblk, c->st);
             launch_reduce_cols(w.rpart, w.rblk, m, w.norms, c->st);
         }
         CK(cudaMemcpyAsync(w.h_norms, w.norms, m * sizeof(double), cudaMemcpyDeviceToHost, c->st));
@@ -651,7 +682,17 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
     int total_steps = 0, restarts = 0, deflations = 0, final_rank = m;
     long long mvms = 0;
     dsbcg_status result = DSBCG_OK;
-    const bool mixed = prec != P64;
+    // right-hand sides of the inner solves: the FP64 fields, or the FP32 hi
+    // planes of the double-float fields
+    const int rprec = hp == PDD ? P32 : P64;
+    const size_t rld = hp_ld(c, hp);
+    auto accumulate = [&](double2* y, const void* x, int nf) {
+        Prof p(c, DSBCG_KCLASS_OTHER);
+        if (hp == PDD)
+            launch_accumulate_pairs((float2*)y, ld, (const float2*)x, ld, nf, n, c->st);
+        else
+            launch_accumulate(work_prec(prec), y, ld, x, ld, nf, n, c->st);
+    };
     const double drop = mixed ? std::max(prm.restart_drop, 1e-12) : 0.0;
 
     // --- joint inner solve on B for all shifts
@@ -660,7 +701,8 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
         for (int j = 0; j < s; ++j)
             for (int i = 0; i < m; ++i) tg[(size_t)j * m + i] = std::max(drop * bn[i], 0.5 * tol * bn[i]);
         InnerResult ir;
-        CKS(inner_solve(c, w.B64, m, sigma, s, tg.data(), prec, dtol, prm.max_block_steps, prm.freeze_converged,
+        CKS(inner_solve(c, w.B64, rprec, rld, m, sigma, s, tg.data(), prec, dtol, prm.max_block_steps,
+                        prm.freeze_converged,
                         prm.poll_every, &ir, 0, conv.data()));
         total_steps += ir.steps;
         mvms += ir.mvms;
@@ -668,10 +710,9 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
         final_rank = ir.final_rank;
         if (ir.status == DSBCG_ERR_NOT_HPD) return DSBCG_ERR_NOT_HPD;
         if (ir.status != 0) return DSBCG_ERR_CUDA;
-        Prof p(c, DSBCG_KCLASS_OTHER);
-        launch_accumulate(work_prec(prec), w.X64, ld, w.Xin, ld, s * m, n, c->st);
+        accumulate(w.X64, w.Xin, s * m);
     }
-    // --- FP64 true residuals and per-shift restarts.  Shift by shift: R_j of
+    // --- high-precision true residuals and per-shift restarts.  Shift by shift: R_j of
     // every column; while some column of shift j is above tol, restart on the
     // unconverged columns of R_j, then recompute the residual of just those
     // columns, which is the right-hand side of the next restart.
@@ -684,7 +725,7 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
     };
     for (int j = 0; j < s; ++j) {
         double2* Xj = w.X64 + (size_t)j * m * ld;
-        CKS(true_residual(c, w.R64, w.B64, Xj, m, sigma[j], r2.data()));
+        CKS(true_residual(c, hp, w.R64, w.B64, Xj, m, sigma[j], r2.data()));
         mvms += m;
         cols.clear();
         for (int i = 0; i < m; ++i) {
@@ -703,7 +744,7 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
             }
             CKS(gather(w.rhs, w.R64, src));
             InnerResult ir;
-            CKS(inner_solve(c, w.rhs, mu, &sigma[j], 1, tg.data(), prec, dtol,
+            CKS(inner_solve(c, w.rhs, rprec, rld, mu, &sigma[j], 1, tg.data(), prec, dtol,
                             std::max(1, prm.max_block_steps - total_steps), prm.freeze_converged, prm.poll_every,
                             &ir, total_steps, conv_tmp.data()));
             total_steps += ir.steps;
@@ -714,14 +755,13 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
             if (ir.status != 0) return DSBCG_ERR_CUDA;
             for (int q = 0; q < mu; ++q) {
                 if (conv_tmp[q] >= 0) conv[(size_t)j * m + cols[q]] = conv_tmp[q];
-                Prof p(c, DSBCG_KCLASS_OTHER);
-                launch_accumulate(work_prec(prec), Xj + (size_t)cols[q] * ld, ld,
-                                  (char*)w.Xin + (size_t)q * ld * prec_elem_bytes(work_prec(prec)), ld, 1, n, c->st);
+                accumulate(Xj + (size_t)cols[q] * ld,
+                           (char*)w.Xin + (size_t)q * ld * prec_elem_bytes(work_prec(prec)), 1);
             }
             // residual of the restarted columns only
             CKS(gather(w.Xg, Xj, cols));
             CKS(gather(w.Bg, w.B64, cols));
-            CKS(true_residual(c, w.R64, w.Bg, w.Xg, mu, sigma[j], r2.data()));
+            CKS(true_residual(c, hp, w.R64, w.Bg, w.Xg, mu, sigma[j], r2.data()));
             mvms += mu;
             std::vector<int> next;
             for (int q = 0; q < mu; ++q) {
@@ -737,31 +777,29 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
         if (!(r <= tol)) result = DSBCG_NOT_CONVERGED;
 
     // --- output X (canonical complex128 [s][m][n])
+    auto unpack = [&](double2* dst, const double2* src, int nf) {
+        Prof p(c, DSBCG_KCLASS_OTHER);
+        if (hp == PDD)
+            launch_unpack_pairs(dst, (const float2*)src, ld, nf, c->V, c->st);
+        else
+            launch_unpack_fields(P64, dst, src, ld, nf, c->V, 1.f, c->st);
+    };
     double2* xcanon = nullptr;
     if (x_dev) {
         xcanon = (double2*)X;
-        {
-            Prof p(c, DSBCG_KCLASS_OTHER);
-            launch_unpack_fields(P64, xcanon, w.X64, ld, s * m, c->V, 1.f, c->st);
-        }
+        unpack(xcanon, w.X64, s * m);
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(c->st));
     } else if (void* xmap = mapped_host_ptr(X)) {
         // pinned host memory mapped into the device address space: the
         // unpack kernel writes the canonical layout straight into it
-        {
-            Prof p(c, DSBCG_KCLASS_OTHER);
-            launch_unpack_fields(P64, (double2*)xmap, w.X64, ld, s * m, c->V, 1.f, c->st);
-        }
+        unpack((double2*)xmap, w.X64, s * m);
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(c->st));
     } else {
         // stage one shift at a time through R64/T64a (m fields each)
         for (int j = 0; j < s; ++j) {
-            {
-                Prof p(c, DSBCG_KCLASS_OTHER);
-                launch_unpack_fields(P64, w.T64a, w.X64 + (size_t)j * m * ld, ld, m, c->V, 1.f, c->st);
-            }
+            unpack(w.T64a, w.X64 + (size_t)j * m * ld, m);
             CK(cudaMemcpyAsync((double2*)X + (size_t)j * m * n, w.T64a, (size_t)m * n * sizeof(double2),
                                cudaMemcpyDeviceToHost, c->st));
         }
