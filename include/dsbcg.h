@@ -52,12 +52,21 @@ typedef enum {
 
 /* Storage precision of spinor fields and links inside the Krylov iteration.
  * Arithmetic on FP32/BF16/FP16 storage is FP32; the m x m block coefficients,
- * deflation, per-shift recurrences and true residuals are always FP64. */
+ * deflation and per-shift recurrences are always FP64.  True residuals and
+ * accumulated solutions are FP64 for FP64 storage and double-float for the
+ * reduced storages.
+ * DSBCG_PREC_DF32 ("double-float"): each real number is an unevaluated sum
+ * hi + lo of two FP32 words (48-bit significand, FP32 exponent range,
+ * arithmetic on the FP32 pipes through error-free transformations).  It is
+ * the arithmetic of the true residuals of reduced-precision solves, offered
+ * to dsbcg_apply / dsbcg_apply_static; it is not a Krylov storage (dsbcg_solve
+ * rejects it). */
 typedef enum {
     DSBCG_PREC_FP64 = 0,
     DSBCG_PREC_FP32 = 1,
     DSBCG_PREC_BF16 = 2,
-    DSBCG_PREC_FP16 = 3
+    DSBCG_PREC_FP16 = 3,
+    DSBCG_PREC_DF32 = 4
 } dsbcg_prec;
 
 /* Operators for dsbcg_apply. */
@@ -129,8 +138,12 @@ dsbcg_status dsbcg_update_gauge(dsbcg_ctx* ctx, const void* gauge);
  * is advanced by short recurrences from a root-free (block) Cholesky
  * factorisation of sigma_j I + T per shift; directions that become linearly
  * dependent are deflated (Sec. 1, Sec. 3).  With FP32/BF16/FP16 storage the
- * Krylov iteration runs in reduced precision inside an FP64 loop that
- * recomputes true residuals and restarts (reliable updates).
+ * Krylov iteration runs in reduced precision inside a loop that recomputes
+ * true residuals in double-float arithmetic (DSBCG_PREC_DF32) and restarts
+ * (reliable updates); with FP64 storage residuals are FP64.  A double-float
+ * residual carries an absolute error of roughly 2^-44 |A| |x|, so it
+ * certifies tol down to about 1e-13 times the condition number of
+ * sigma_j I + A.
  *   m:     number of right-hand sides, 1 <= m <= 32
  *   B:     device or host complex128 [m][n]
  *   s:     number of shifts, 1 <= s <= 64
@@ -139,14 +152,15 @@ dsbcg_status dsbcg_update_gauge(dsbcg_ctx* ctx, const void* gauge);
  *   X:     device or host complex128 [s][m][n]; output (its input value is ignored)
  *   params: NULL for defaults
  *   stats: NULL or caller-owned
- * Returns DSBCG_OK when every true FP64 relative residual meets tol,
+ * Returns DSBCG_OK when every true relative residual meets tol,
  * DSBCG_NOT_CONVERGED (X still written) when a cap is hit. */
 dsbcg_status dsbcg_solve(dsbcg_ctx* ctx, int m, const void* B, int s, const double* sigma,
                          double tol, const dsbcg_params* params, void* X, dsbcg_stats* stats);
 
 /* Apply D, D^H or A to m fields: out_i = op(in_i).  The fields are converted
- * to `storage` precision, the stencil runs in that precision (FP32
- * arithmetic for reduced precisions), and the result is converted back.
+ * to `storage` precision (any dsbcg_prec, including DSBCG_PREC_DF32), the
+ * stencil runs in that precision (FP32 arithmetic for FP32/BF16/FP16,
+ * double-float for DF32), and the result is converted back.
  *   in, out: device or host complex128 [m][n]; they may not overlap. */
 dsbcg_status dsbcg_apply(dsbcg_ctx* ctx, int op, int storage, int m, const void* in, void* out);
 

@@ -171,6 +171,42 @@ __device__ __forceinline__ ddc cscale(ddc a, dd s) {
     return ddc{dd(a.x.hi * s.hi, a.x.lo * s.hi), dd(a.y.hi * s.hi, a.y.lo * s.hi)};
 }
 
+// Complex double-float helpers for accumulation chains (the stencil): sums
+// stay unnormalised (hi = running FP32 sum, lo = its accumulated rounding
+// errors and low words; the value is hi + lo), each product enters through
+// two_prod plus the cross terms, and the caller normalises once at the end.
+// These overloads take precedence over the generic complex templates.
+__device__ __forceinline__ dd add_nn(dd a, dd b) {
+    float s, t;
+    two_sum(a.hi, b.hi, s, t);
+    return dd(s, t + (a.lo + b.lo));
+}
+// acc += a * b, unnormalised
+__device__ __forceinline__ void fma_nn(dd& acc, dd a, dd b) {
+    float p = a.hi * b.hi;
+    float q = fmaf(a.hi, b.hi, -p);
+    q = fmaf(a.hi, b.lo, q);
+    q = fmaf(a.lo, b.hi, q);
+    float s, t;
+    two_sum(acc.hi, p, s, t);
+    acc = dd(s, acc.lo + (t + q));
+}
+__device__ __forceinline__ dd normalize(dd a) { return quick_two_sum(a.hi, a.lo); }
+__device__ __forceinline__ ddc cadd(ddc a, ddc b) { return ddc{add_nn(a.x, b.x), add_nn(a.y, b.y)}; }
+__device__ __forceinline__ ddc csub(ddc a, ddc b) { return ddc{add_nn(a.x, -b.x), add_nn(a.y, -b.y)}; }
+__device__ __forceinline__ void cfma(ddc& acc, ddc a, ddc b) {
+    fma_nn(acc.x, a.x, b.x);
+    fma_nn(acc.x, -a.y, b.y);
+    fma_nn(acc.y, a.x, b.y);
+    fma_nn(acc.y, a.y, b.x);
+}
+__device__ __forceinline__ void cfmac(ddc& acc, ddc a, ddc b) {
+    fma_nn(acc.x, a.x, b.x);
+    fma_nn(acc.x, a.y, b.y);
+    fma_nn(acc.y, a.x, b.y);
+    fma_nn(acc.y, -a.y, b.x);
+}
+
 template <> struct Tr<PDD> {
     using S2 = float2;             // one word plane of a complex element
     using R = dd;

@@ -215,7 +215,7 @@ __device__ __forceinline__ void su3_mul(const typename Tr<P>::S2* __restrict__ u
 }
 
 template <int P>
-__global__ void __launch_bounds__(32, P == PDD ? 8 : 16) dslash_kernel(typename Tr<P>::S2* __restrict__ out,
+__global__ void __launch_bounds__(32, P == PDD ? 12 : 16) dslash_kernel(typename Tr<P>::S2* __restrict__ out,
                                                    const typename Tr<P>::S2* __restrict__ in,
                                                    size_t ld, const typename Tr<P>::S2* __restrict__ links,
                                                    Geom g, typename Tr<P>::R kappa, int g5in, int g5out,
@@ -316,6 +316,10 @@ __global__ void __launch_bounds__(32, P == PDD ? 8 : 16) dslash_kernel(typename 
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 C v = cscale(p[sp * 3 + a], sgi);
+                if constexpr (P == PDD) {      // close the unnormalised accumulation chains
+                    acc[sp][a].x = normalize(acc[sp][a].x);
+                    acc[sp][a].y = normalize(acc[sp][a].y);
+                }
                 v.x = fma(-kappa, acc[sp][a].x, v.x);
                 v.y = fma(-kappa, acc[sp][a].y, v.y);
                 p[sp * 3 + a] = cscale(v, sgo);

@@ -266,6 +266,20 @@ void prof_collect(dsbcg_ctx* c) {
 // is an FP32 hi plane and an FP32 lo plane of ld complex each.
 inline size_t hp_ld(const dsbcg_ctx* c, int hp) { return hp == PDD ? 2 * c->ld : c->ld; }
 
+// canonical complex128 fields <-> internal fields of any precision
+void pack_any(dsbcg_ctx* c, int p, void* dst, const double2* src, int m) {
+    if (p == PDD)
+        launch_pack_pairs((float2*)dst, c->ld, src, m, c->V, c->st);
+    else
+        launch_pack_fields(p, dst, c->ld, src, m, c->V, c->hscale, c->st);
+}
+void unpack_any(dsbcg_ctx* c, int p, double2* dst, const void* src, int m) {
+    if (p == PDD)
+        launch_unpack_pairs(dst, (const float2*)src, c->ld, m, c->V, c->st);
+    else
+        launch_unpack_fields(p, dst, src, c->ld, m, c->V, c->hscale, c->st);
+}
+
 // out = A in for nf high-precision fields (tmp receives D in)
 void apply_Ahp(dsbcg_ctx* c, int hp, void* out, const void* in, void* tmp, int nf) {
     {
@@ -547,11 +561,11 @@ dsbcg_status dsbcg_set_profiling(dsbcg_ctx* c, int on) {
 }
 
 dsbcg_status dsbcg_apply(dsbcg_ctx* c, int op, int storage, int m, const void* in, void* out) {
-    if (!c || !in || !out || m < 1 || m > 4096 || op < 0 || op > 2 || storage < 0 || storage > 3)
+    if (!c || !in || !out || m < 1 || m > 4096 || op < 0 || op > 2 || storage < 0 || storage > PDD)
         return DSBCG_ERR_ARG;
     CKS(ensure_links(c, storage));
-    const size_t n = c->n, ld = c->ld;
-    const size_t fb = prec_elem_bytes(storage) * ld;
+    const size_t n = c->n, ld = hp_ld(c, storage);
+    const size_t fb = prec_elem_bytes(storage) * c->ld;
     void *a = nullptr, *b = nullptr, *t = nullptr;
     double2 *din = nullptr, *dout = nullptr;
     const bool in_dev = is_device_ptr(in), out_dev = is_device_ptr(out);
@@ -571,7 +585,7 @@ dsbcg_status dsbcg_apply(dsbcg_ctx* c, int op, int storage, int m, const void* i
     if (rs == DSBCG_OK) {
         const double2* src = in_dev ? (const double2*)in : din;
         double2* dst = out_dev ? (double2*)out : dout;
-        launch_pack_fields(storage, a, ld, src, m, c->V, c->hscale, c->st);
+        pack_any(c, storage, a, src, m);
         if (op == DSBCG_OP_D) {
             Prof p(c, DSBCG_KCLASS_DSLASH);
             launch_dslash(storage, b, a, ld, c->links[storage], c->g, c->kappa, 0, 0, nullptr, m, m, c->hscale, c->st);
@@ -587,7 +601,7 @@ dsbcg_status dsbcg_apply(dsbcg_ctx* c, int op, int storage, int m, const void* i
             Prof p(c, DSBCG_KCLASS_DSLASH);
             launch_dslash(storage, b, t, ld, c->links[storage], c->g, c->kappa, 1, 1, nullptr, m, m, c->hscale, c->st);
         }
-        launch_unpack_fields(storage, dst, b, ld, m, c->V, c->hscale, c->st);
+        unpack_any(c, storage, dst, b, m);
         if (!out_dev) cudaMemcpyAsync(out, dout, m * n * sizeof(double2), cudaMemcpyDeviceToHost, c->st);
         if (cudaGetLastError() != cudaSuccess) fail(DSBCG_ERR_CUDA);
         if (cudaStreamSynchronize(c->st) != cudaSuccess) fail(DSBCG_ERR_CUDA);
@@ -647,10 +661,7 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
     {
         Prof p(c, DSBCG_KCLASS_OTHER, 2);
         launch_check_finite(bcanon, (size_t)m * n, w.flag, c->st);
-        if (hp == PDD)
-            launch_pack_pairs((float2*)w.B64, ld, bcanon, m, c->V, c->st);
-        else
-            launch_pack_fields(P64, w.B64, ld, bcanon, m, c->V, 1.f, c->st);
+        pack_any(c, hp, w.B64, bcanon, m);
     }
     int hflag = 0;
     CK(cudaMemcpyAsync(&hflag, w.flag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
@@ -779,10 +790,7 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
     // --- output X (canonical complex128 [s][m][n])
     auto unpack = [&](double2* dst, const double2* src, int nf) {
         Prof p(c, DSBCG_KCLASS_OTHER);
-        if (hp == PDD)
-            launch_unpack_pairs(dst, (const float2*)src, ld, nf, c->V, c->st);
-        else
-            launch_unpack_fields(P64, dst, src, ld, nf, c->V, 1.f, c->st);
+        unpack_any(c, hp, dst, src, nf);
     };
     double2* xcanon = nullptr;
     if (x_dev) {
@@ -924,11 +932,11 @@ dsbcg_status static_scratch_address(void** out) {
 }  // namespace
 
 extern "C" dsbcg_status dsbcg_apply_static(dsbcg_ctx* c, int op, int storage, int m, const void* in, void* out) {
-    if (!c || !in || !out || m < 1 || op < 0 || op > 2 || storage < 0 || storage > 3) return DSBCG_ERR_ARG;
+    if (!c || !in || !out || m < 1 || op < 0 || op > 2 || storage < 0 || storage > PDD) return DSBCG_ERR_ARG;
     if (!is_device_ptr(in) || !is_device_ptr(out)) return DSBCG_ERR_ARG;
     if (!c->links[storage]) return DSBCG_ERR_UNSUPPORTED;
-    const size_t ld = c->ld;
-    const size_t fb = prec_elem_bytes(storage) * ld;
+    const size_t ld = hp_ld(c, storage);
+    const size_t fb = prec_elem_bytes(storage) * c->ld;
     const size_t nbuf = op == DSBCG_OP_A ? 3 : 2;
     if ((size_t)m > (size_t)DSBCG_STATIC_SCRATCH_BYTES / (nbuf * fb)) return DSBCG_ERR_ARG;
     void* base = nullptr;
@@ -938,7 +946,7 @@ extern "C" dsbcg_status dsbcg_apply_static(dsbcg_ctx* c, int op, int storage, in
     char* t = b + (size_t)m * fb;
     const double2* src = (const double2*)in;
     double2* dst = (double2*)out;
-    launch_pack_fields(storage, a, ld, src, m, c->V, c->hscale, c->st);
+    pack_any(c, storage, a, src, m);
     if (op == DSBCG_OP_D) {
         launch_dslash(storage, b, a, ld, c->links[storage], c->g, c->kappa, 0, 0, nullptr, m, m, c->hscale, c->st);
     } else if (op == DSBCG_OP_DDAG) {
@@ -947,7 +955,7 @@ extern "C" dsbcg_status dsbcg_apply_static(dsbcg_ctx* c, int op, int storage, in
         launch_dslash(storage, t, a, ld, c->links[storage], c->g, c->kappa, 0, 0, nullptr, m, m, c->hscale, c->st);
         launch_dslash(storage, b, t, ld, c->links[storage], c->g, c->kappa, 1, 1, nullptr, m, m, c->hscale, c->st);
     }
-    launch_unpack_fields(storage, dst, b, ld, m, c->V, c->hscale, c->st);
+    unpack_any(c, storage, dst, b, m);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(c->st));
     return DSBCG_OK;

@@ -24,7 +24,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdsbcg.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "dsbcg.h")
 
-PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3}
+PREC = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3, "df32": 4}
 OPS = {"D": 0, "Ddag": 1, "A": 2}
 STATUS = {0: "OK", 1: "NOT_CONVERGED", -1: "ERR_ARG", -2: "ERR_NOT_HPD", -3: "ERR_CUDA",
           -4: "ERR_OOM", -5: "ERR_NONFINITE", -6: "ERR_UNSUPPORTED"}

@@ -13,7 +13,8 @@ from paper_1205_0359_gb300 import dsbcg, synth
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-13, "fp32": 2e-6, "fp16": 4e-3, "bf16": 3e-2}
+# df32: double-float pairs (48-bit significands), a few 2^-48 per operation
+TOL = {"fp64": 1e-13, "df32": 5e-13, "fp32": 2e-6, "fp16": 4e-3, "bf16": 3e-2}
 
 
 def _setup(dims, m, seed, eps=0.7, kappa=0.13):
@@ -25,7 +26,7 @@ def _setup(dims, m, seed, eps=0.7, kappa=0.13):
 
 
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (2, 4, 6, 5), (2, 2, 2, 2), (8, 4, 4, 6)])
-@pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("storage", ["fp64", "df32", "fp32", "fp16", "bf16"])
 def test_operators_match_oracle(dims, storage):
     m = 5
     U, F, kappa = _setup(dims, m, 17)
@@ -46,7 +47,7 @@ def test_multi_rhs_equals_single_rhs_bitwise():
     dev = torch.device("cuda")
     ctx = dsbcg.Context(dims, torch.from_numpy(U).to(dev), kappa)
     Ft = torch.from_numpy(F).to(dev)
-    for storage in ("fp64", "fp32"):
+    for storage in ("fp64", "df32", "fp32"):
         many = ctx.apply("A", Ft, storage=storage)
         for i in (0, 7, 11):
             one = ctx.apply("A", Ft[i:i + 1].contiguous(), storage=storage)
