@@ -61,8 +61,9 @@ namespace {
 // __syncwarp: the matrices are at most 32 x 32, so one warp has enough
 // parallelism and block-wide barriers would dominate the run time.
 constexpr int WS = 32;
-constexpr int NT = 128;            // threads of the CTAs that also reduce partial sums
+constexpr int NT = 256;            // threads of the CTAs that also reduce partial sums
 constexpr int GSL = 36;            // slots per 4 x 4 tile in the Gram partials
+constexpr int RED_MAX = 1024;      // group sums held in shared memory by reduce_partials
 
 __device__ __forceinline__ double2 z2() { return make_double2(0.0, 0.0); }
 __device__ __forceinline__ double2 conjd(double2 a) { return make_double2(a.x, -a.y); }
@@ -170,19 +171,22 @@ __device__ int pivoted_qr(const double2* G, int ld, int n, const double* ref, do
     wsync();
     int rank = n;
     for (int p = 0; p < n; ++p) {
-        // pivot choice: every lane scans the same (short) candidate list
+        // pivot choice: every lane scans the same (short) candidate list;
+        // dd[q] / ref[q] > dd[b] / ref[b] is tested as dd[q] ref[b] >
+        // dd[b] ref[q] (both refs > 0), without FP64 divisions (slow on GB300)
         int best = -1;
-        double bv = -1.0;
+        double bd = 0.0, br = 1.0;
         for (int q = p; q < n; ++q) {
-            double r = ref[perm[q]];
-            double v = (r > 0.0) ? dd[q] / r : -1.0;
-            if (v > bv) {
-                bv = v;
+            const double r = ref[perm[q]];
+            if (!(r > 0.0)) continue;
+            if (best < 0 || dd[q] * br > bd * r) {
+                bd = dd[q];
+                br = r;
                 best = q;
             }
         }
         wsync();
-        if (best < 0 || !(bv > dtol * dtol) || !(dd[best] > 0.0)) {
+        if (best < 0 || !(bd > dtol * dtol * br) || !(dd[best] > 0.0)) {
             rank = p;
             break;
         }
@@ -203,6 +207,7 @@ __device__ int pivoted_qr(const double2* G, int ld, int n, const double* ref, do
             wsync();
         }
         const double rpp = sqrt(dd[p]);
+        const double irpp = 1.0 / rpp;
         const int gp = perm[p];
         if (threadIdx.x == 0) Rm[p * n + p] = make_double2(rpp, 0.0);
         for (int r = p + 1 + threadIdx.x; r < n; r += WS) {
@@ -213,7 +218,7 @@ __device__ int pivoted_qr(const double2* G, int ld, int n, const double* ref, do
                 s.x -= a.x * b.x - a.y * b.y;
                 s.y -= a.x * b.y + a.y * b.x;
             }
-            s = make_double2(s.x / rpp, s.y / rpp);
+            s = make_double2(s.x * irpp, s.y * irpp);
             Rm[p * n + r] = s;
             dd[r] -= s.x * s.x + s.y * s.y;
         }
@@ -227,6 +232,9 @@ __device__ int pivoted_qr(const double2* G, int ld, int n, const double* ref, do
     }
     wsync();
     // S = Pi_r R11^{-1}: lane c solves R11 y = e_c by back substitution
+    // (diagonal reciprocals formed once, in dd[])
+    for (int i = threadIdx.x; i < rank; i += WS) dd[i] = 1.0 / Rm[i * n + i].x;
+    wsync();
     for (int c = threadIdx.x; c < rank; c += WS) {
         for (int i = c; i >= 0; --i) {
             double2 s = (i == c) ? make_double2(1.0, 0.0) : z2();
@@ -235,8 +243,8 @@ __device__ int pivoted_qr(const double2* G, int ld, int n, const double* ref, do
                 s.x -= a.x * b.x - a.y * b.y;
                 s.y -= a.x * b.y + a.y * b.x;
             }
-            double d = Rm[i * n + i].x;
-            S[perm[i] * ld + c] = make_double2(s.x / d, s.y / d);
+            const double id = dd[i];
+            S[perm[i] * ld + c] = make_double2(s.x * id, s.y * id);
         }
     }
     wsync();
@@ -263,44 +271,87 @@ __device__ inline void tile_ij(int t, int T, int herm, int* ti, int* tj) {
 // With reduced-precision storage the partials are FP32 (they carry FP32
 // accuracy) and are summed with compensated (Kahan) FP32 additions, which
 // cost far less than FP64 ones on GB300; FP64 storage sums in FP64.
+// write the reduced slot `it` ([tile][36] order) into G / diag
+__device__ __forceinline__ void reduce_store(double2* G, int ld, double* diag, int T, int herm, int nf_max, int it,
+                                             double s) {
+    const int tile = it / GSL, q = it % GSL;
+    int ti, tj;
+    tile_ij(tile, T, herm, &ti, &tj);
+    if (q < 32) {
+        const int i = ti * 4 + ((q >> 1) >> 2), j = tj * 4 + ((q >> 1) & 3);
+        if (i < nf_max && j < nf_max) {
+            if (q & 1) {
+                G[i * ld + j].y = s;
+                if (herm && ti != tj) G[j * ld + i].y = -s;
+            } else {
+                G[i * ld + j].x = s;
+                if (herm && ti != tj) G[j * ld + i].x = s;
+            }
+        }
+    } else if (diag && ti == tj) {
+        const int j = tj * 4 + (q - 32);
+        if (j < nf_max) diag[j] = s;
+    }
+}
+
 __device__ void reduce_partials(const double* __restrict__ part, int nblk, int nf_max, int herm, double2* G, int ld,
                                 double* diag, int fp64) {
     const int T = (nf_max + 3) / 4;
     const int ntiles = herm ? T * (T + 1) / 2 : T * T;
-    for (int u = threadIdx.x; u < ntiles * GSL; u += blockDim.x) {
-        const int tile = u / GSL, q = u % GSL;
+    const int items = ntiles * GSL;
+    // consecutive threads take consecutive slots (coalesced rows of 36); when
+    // the CTA has threads to spare, ng groups split the CTAs' range and their
+    // sums are added in group order; four interleaved accumulators per
+    // thread keep several loads in flight.  Fixed order: bitwise reproducible.
+    __shared__ double red[RED_MAX];
+    const int ng = max(1, min((int)blockDim.x / items, RED_MAX / items));
+    const int chunk = (nblk + ng - 1) / ng;
+    for (int u = threadIdx.x; u < items * ng; u += blockDim.x) {
+        const int it = u % items, grp = u / items;
+        const int b0 = grp * chunk, b1 = min(nblk, b0 + chunk);
+        const int tile = it / GSL, q = it % GSL;
         const size_t off = (size_t)tile * nblk * GSL + q;
         double s = 0.0;
         if (fp64) {
             const double* p = part + off;
-            for (int b = 0; b < nblk; ++b) s += p[(size_t)b * GSL];
+            double a[4] = {0.0, 0.0, 0.0, 0.0};
+            int b = b0;
+            for (; b + 4 <= b1; b += 4)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) a[r] += p[(size_t)(b + r) * GSL];
+            for (; b < b1; ++b) a[0] += p[(size_t)b * GSL];
+            s = (a[0] + a[1]) + (a[2] + a[3]);
         } else {
             const float* p = reinterpret_cast<const float*>(part) + off;
-            float sum = 0.f, comp = 0.f;
-            for (int b = 0; b < nblk; ++b) {
-                const float y = p[(size_t)b * GSL] - comp;
-                const float t = sum + y;
-                comp = (t - sum) - y;
-                sum = t;
-            }
-            s = (double)sum - (double)comp;
-        }
-        int ti, tj;
-        tile_ij(tile, T, herm, &ti, &tj);
-        if (q < 32) {
-            const int i = ti * 4 + ((q >> 1) >> 2), j = tj * 4 + ((q >> 1) & 3);
-            if (i < nf_max && j < nf_max) {
-                if (q & 1) {
-                    G[i * ld + j].y = s;
-                    if (herm && ti != tj) G[j * ld + i].y = -s;
-                } else {
-                    G[i * ld + j].x = s;
-                    if (herm && ti != tj) G[j * ld + i].x = s;
+            float sum[4] = {0.f, 0.f, 0.f, 0.f}, comp[4] = {0.f, 0.f, 0.f, 0.f};
+            int b = b0;
+            for (; b + 4 <= b1; b += 4) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const float y = p[(size_t)(b + r) * GSL] - comp[r];
+                    const float t = sum[r] + y;
+                    comp[r] = (t - sum[r]) - y;
+                    sum[r] = t;
                 }
             }
-        } else if (diag && ti == tj) {
-            const int j = tj * 4 + (q - 32);
-            if (j < nf_max) diag[j] = s;
+            for (; b < b1; ++b) {
+                const float y = p[(size_t)b * GSL] - comp[0];
+                const float t = sum[0] + y;
+                comp[0] = (t - sum[0]) - y;
+                sum[0] = t;
+            }
+            s = ((double)sum[0] - (double)comp[0]) + ((double)sum[1] - (double)comp[1]) +
+                (((double)sum[2] - (double)comp[2]) + ((double)sum[3] - (double)comp[3]));
+        }
+        if (ng > 1) red[grp * items + it] = s;
+        else reduce_store(G, ld, diag, T, herm, nf_max, it, s);
+    }
+    if (ng > 1) {
+        __syncthreads();
+        for (int it = threadIdx.x; it < items; it += blockDim.x) {
+            double s = 0.0;
+            for (int g = 0; g < ng; ++g) s += red[g * items + it];
+            reduce_store(G, ld, diag, T, herm, nf_max, it, s);
         }
     }
 }
