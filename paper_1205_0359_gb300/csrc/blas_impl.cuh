@@ -266,19 +266,17 @@ __global__ void __launch_bounds__(256) init_basis_kernel(typename Tr<P>::S2* __r
 }
 
 // ---------------------------------------------------------------------------
-// Fused shift update (the per-shift short recurrences of Sec. 3 for all
-// shifts in one pass over HBM):
-//     V_{k+1} = W S;  for every active shift j:
-//     X_j += P_j Ut_j,   P_j <- V_{k+1} - P_j Lh_j.
-// One thread per row e, ROWS rows per CTA.  The row tile of V_{k+1} stays in
-// shared memory across the shift loop.  The P_j and X_j tiles (one
-// contiguous ROWS-element run per field) are streamed with bulk asynchronous
-// copies (cp.async.bulk, completion on an mbarrier), double-buffered: while
-// shift j is computed, the tiles of the next active shift are in flight, and
-// the updated tiles of the previous one are written back with bulk stores.
-// Every mbarrier wait is bounded; on timeout the kernel records an error in
-// the control block, drains its own copies and returns.  For the first step
-// of an inner solve (k == 1) the search block is P_j = V_1 itself.
+// Shift update (the per-shift short recurrences of Sec. 3 for all shifts,
+// one pass over HBM per operand):
+//     V_{k+1} = W S                       (v_update_kernel, one thread per row)
+//     for every active shift j:
+//     X_j += P_j Ut_j,   P_j <- V_{k+1} - P_j Lh_j   (shift_tile_kernel)
+// shift_tile_kernel runs one CTA per (row tile, shift); its tiles arrive by
+// bulk asynchronous copies (cp.async.bulk, completion on an mbarrier) and
+// each thread updates two rows.  Every mbarrier wait is bounded; on timeout
+// the kernel records an error in the control block, drains its own copies
+// and returns.  For the first step of an inner solve (k == 1) the search
+// block is P_j = V_1 itself.
 constexpr int ST_WAIT_TIMEOUT = -3;        // reported to the host as DSBCG_ERR_CUDA
 constexpr long MBAR_SPIN_LIMIT = 1L << 22;
 
@@ -565,8 +563,13 @@ __host__ __device__ constexpr size_t su_smem_bytes(int rows) {
            + 2 * (size_t)NF * NF * sizeof(typename Tr<PW>::C) + 16;
 }
 
+// rows per thread of shift_tile_kernel: one (two rows per thread halve the
+// shared-memory coefficient reads but, at about 170 registers, cut the
+// resident warps from 28 to 10 per SM, which measured slower on GB300)
+__host__ __device__ constexpr int su_rpt(int, int) { return 1; }
+
 template <int P, int PW, int NF, int ROWS>
-__global__ void __launch_bounds__(ROWS) shift_tile_kernel(
+__global__ void __launch_bounds__(ROWS / su_rpt(NF, PW)) shift_tile_kernel(
     const typename Tr<P>::S2* __restrict__ Vn, const typename Tr<P>::S2* __restrict__ Vk, size_t ld,
     typename Tr<PW>::S2* __restrict__ Pb, typename Tr<PW>::S2* __restrict__ Xb, size_t ldw, size_t n, int s, int m,
     Ctl* __restrict__ ctl, const typename Tr<PW>::C* __restrict__ cU, const typename Tr<PW>::C* __restrict__ cL,
@@ -612,7 +615,7 @@ __global__ void __launch_bounds__(ROWS) shift_tile_kernel(
         }
         for (int i = 0; i < m; ++i) bulk_g2s(sX + i * ROWS, Xj + (size_t)i * ldw, tb, bar);
     }
-    for (int t = tid; t < NF * NF; t += ROWS) {
+    for (int t = tid; t < NF * NF; t += ROWS / su_rpt(NF, PW)) {
         sU[t] = cU[((size_t)j * M_MAX + t / NF) * M_MAX + t % NF];
         sL[t] = cL[((size_t)j * M_MAX + t / NF) * M_MAX + t % NF];
     }
@@ -625,34 +628,91 @@ __global__ void __launch_bounds__(ROWS) shift_tile_kernel(
         }
         return;
     }
-    if (tid >= rows) return;
     const float inv = (P == PBF16 || P == PF16) ? 1.f / hscale : 1.f;
-    auto ldv = [&](const SE* base, int c) -> C {
-        auto q = Elem<P>::ld(base, (size_t)c * ROWS + tid, inv);
+    auto ldv = [&](const SE* base, int c, int r) -> C {
+        auto q = Elem<P>::ld(base, (size_t)c * ROWS + r, inv);
         return mk(R(q.x), R(q.y));
     };
-    C t[NF], x[NF];
+    // RPT rows per thread (r = tid, tid + ROWS / RPT, ...): every coefficient
+    // read from shared memory serves all of them, and FP32 coefficients are
+    // read two at a time; each element accumulates over a in ascending order
+    constexpr int RPT = su_rpt(NF, PW), TPB = ROWS / RPT;
+    int rr_[RPT];
+    bool ok_[RPT];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+        rr_[q] = tid + q * TPB;
+        ok_[q] = rr_[q] < rows;
+    }
+    C t[RPT][NF], x[RPT][NF];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q)
+#pragma unroll
+        for (int a = 0; a < NF; ++a) {
+            const int r = ok_[q] ? rr_[q] : 0;
+            if (a < mk_) t[q][a] = (k == 1) ? ldv(reinterpret_cast<const SE*>(sP), a, r) : sP[a * ROWS + r];
+            else t[q][a] = mk(R(0), R(0));
+            x[q][a] = a < m ? sX[a * ROWS + r] : mk(R(0), R(0));
+        }
+    // X_j += P_j Ut_j
 #pragma unroll
     for (int a = 0; a < NF; ++a) {
-        if (a < mk_) t[a] = (k == 1) ? ldv(reinterpret_cast<const SE*>(sP), a) : sP[a * ROWS + tid];
-        else t[a] = mk(R(0), R(0));
-        x[a] = a < m ? sX[a * ROWS + tid] : mk(R(0), R(0));
-    }
 #pragma unroll
-    for (int i = 0; i < NF; ++i) {
+        for (int i = 0; i < NF; i += 2) {
+            C u0, u1;
+            if constexpr (sizeof(C) == 8) {
+                const float4 u2 = *reinterpret_cast<const float4*>(&sU[a * NF + i]);
+                u0 = mk(R(u2.x), R(u2.y));
+                u1 = mk(R(u2.z), R(u2.w));
+            } else {
+                u0 = sU[a * NF + i];
+                u1 = sU[a * NF + i + 1];
+            }
 #pragma unroll
-        for (int a = 0; a < NF; ++a) cfma(x[i], t[a], sU[a * NF + i]);
-        if (i < m) Xj[(size_t)i * ldw + tid] = x[i];
-    }
-#pragma unroll
-    for (int c = 0; c < NF; ++c) {
-        if (c < mn) {
-            C p = ldv(sV, c);
-#pragma unroll
-            for (int a = 0; a < NF; ++a) cfms(p, t[a], sL[a * NF + c]);
-            Pjw[(size_t)c * ldw + tid] = p;
+            for (int q = 0; q < RPT; ++q) {
+                cfma(x[q][i], t[q][a], u0);
+                cfma(x[q][i + 1], t[q][a], u1);
+            }
         }
     }
+#pragma unroll
+    for (int q = 0; q < RPT; ++q)
+        if (ok_[q])
+#pragma unroll
+            for (int i = 0; i < NF; ++i)
+                if (i < m) Xj[(size_t)i * ldw + rr_[q]] = x[q][i];
+    // P_j <- V_{k+1} - P_j Lh_j
+    C pn[RPT][NF];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q)
+#pragma unroll
+        for (int c = 0; c < NF; ++c) pn[q][c] = c < mn ? ldv(sV, c, ok_[q] ? rr_[q] : 0) : mk(R(0), R(0));
+#pragma unroll
+    for (int a = 0; a < NF; ++a) {
+#pragma unroll
+        for (int c = 0; c < NF; c += 2) {
+            C l0, l1;
+            if constexpr (sizeof(C) == 8) {
+                const float4 l2 = *reinterpret_cast<const float4*>(&sL[a * NF + c]);
+                l0 = mk(R(l2.x), R(l2.y));
+                l1 = mk(R(l2.z), R(l2.w));
+            } else {
+                l0 = sL[a * NF + c];
+                l1 = sL[a * NF + c + 1];
+            }
+#pragma unroll
+            for (int q = 0; q < RPT; ++q) {
+                cfms(pn[q][c], t[q][a], l0);
+                cfms(pn[q][c + 1], t[q][a], l1);
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < RPT; ++q)
+        if (ok_[q])
+#pragma unroll
+            for (int c = 0; c < NF; ++c)
+                if (c < mn) Pjw[(size_t)c * ldw + rr_[q]] = pn[q][c];
 }
 
 inline int nf_bucket(int nf) { return nf <= 4 ? 4 : nf <= 8 ? 8 : nf <= 12 ? 12 : nf <= 16 ? 16 : nf <= 24 ? 24 : 32; }
@@ -722,7 +782,7 @@ void launch_su_t(void* Vnext, const void* W, const void* Vk, size_t ld, void* Pp
             attr = true;                                                                                    \
         }                                                                                                   \
         const unsigned g = (unsigned)(((n + ROWS - 1) / ROWS) * (size_t)s);                                 \
-        shift_tile_kernel<P, PW, NF, ROWS><<<g, ROWS, SMEM, st>>>(                                          \
+        shift_tile_kernel<P, PW, NF, ROWS><<<g, ROWS / su_rpt(NF, PW), SMEM, st>>>(                                          \
             (const S2*)Vnext, (const S2*)Vk, ld, (W2*)Pp, (W2*)X, ldw, n, s, m, ctl, (const CW*)coefU,      \
             (const CW*)coefL, active, hscale);                                                              \
     }
