@@ -29,6 +29,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <deque>
 #include <mutex>
 #include <vector>
 
@@ -47,6 +48,34 @@ struct DevBuf {
 struct KEvent {
     int cls;
     cudaEvent_t a, b;
+};
+
+// One inner solve (one block Lanczos process with s_in shifts): its device
+// buffers, control block and stream.  Lane 0 is the joint solve of all shifts
+// on the context's stream; the per-shift restarts of the refinement loop run
+// on lane 0 and on further one-shift lanes with their own streams, so that
+// the m x m kernels of one restart (latency-bound) overlap the streaming
+// kernels of the others.
+struct Lane {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ready = nullptr;                  // own lanes: main-stream work they wait for
+    void *vring = nullptr, *zw = nullptr, *y = nullptr, *P = nullptr, *Xin = nullptr;
+    double2* rhs = nullptr;                       // gathered right-hand sides (high precision)
+    double* partials = nullptr;
+    int nblk = 0;
+    dsbcg::SmallState* ss = nullptr;
+    dsbcg::Ctl* ctl = nullptr;
+    double2* G = nullptr;
+    double* diag = nullptr;
+    void *coef_a = nullptr, *coef_bh = nullptr, *coefS = nullptr, *coefU = nullptr, *coefL = nullptr;
+    int *active = nullptr, *conv_step = nullptr;
+    double *res = nullptr, *sigma = nullptr, *target = nullptr;
+    dsbcg::Ctl* h_ctl = nullptr;                  // pinned
+    int* h_conv = nullptr;                        // pinned
+    // the inner solve in progress
+    int m_in = 0, s_in = 0, prec = 0, step = 0, max_steps = 0, freeze = 0, poll_every = 1;
+    double dtol = 0;
+    bool running = false;
 };
 
 }  // namespace
@@ -88,6 +117,8 @@ struct dsbcg_ctx {
         int* h_conv = nullptr;           // pinned
         int nblk = 0, rblk = 0;
         std::vector<void*> mem;
+        std::vector<Lane> lanes;        // [0]: the joint solve's buffers; then refinement lanes
+        std::vector<void*> pinned;      // refinement lanes' pinned words
     } ws;
 };
 
@@ -143,6 +174,14 @@ dsbcg_status dmalloc(dsbcg_ctx* c, void** p, size_t bytes) {
 
 void free_ws(dsbcg_ctx* c) {
     cudaStreamSynchronize(c->st);
+    for (auto& L : c->ws.lanes) {
+        if (L.st && L.st != c->st) {
+            cudaStreamSynchronize(L.st);
+            cudaStreamDestroy(L.st);
+        }
+        if (L.ready) cudaEventDestroy(L.ready);
+    }
+    for (void* p : c->ws.pinned) cudaFreeHost(p);
     for (void* p : c->ws.mem) cudaFree(p);
     c->ws.mem.clear();
     if (c->ws.h_ctl) cudaFreeHost(c->ws.h_ctl);
@@ -214,7 +253,88 @@ dsbcg_status ensure_ws(dsbcg_ctx* c, int m, int s, int prec) {
     w.m = m;
     w.s = s;
     w.prec = prec;
+    Lane L0;
+    L0.st = c->st;
+    L0.vring = w.vring;
+    L0.zw = w.zw;
+    L0.y = w.y;
+    L0.P = w.P;
+    L0.Xin = w.Xin;
+    L0.rhs = w.rhs;
+    L0.partials = w.partials;
+    L0.nblk = w.nblk;
+    L0.ss = w.ss;
+    L0.ctl = w.ctl;
+    L0.G = w.G;
+    L0.diag = w.diag;
+    L0.coef_a = w.coef_a;
+    L0.coef_bh = w.coef_bh;
+    L0.coefS = w.coefS;
+    L0.coefU = w.coefU;
+    L0.coefL = w.coefL;
+    L0.active = w.active;
+    L0.conv_step = w.conv_step;
+    L0.res = w.res;
+    L0.sigma = w.sigma;
+    L0.target = w.target;
+    L0.h_ctl = w.h_ctl;
+    L0.h_conv = w.h_conv;
+    w.lanes.assign(1, L0);
     return DSBCG_OK;
+}
+
+// Add one-shift refinement lanes until there are `want` lanes (lane 0
+// included) or device memory runs out; returns the number available.
+int ensure_refine_lanes(dsbcg_ctx* c, int want) {
+    auto& w = c->ws;
+    const int m = w.m, prec = w.prec;
+    const size_t fb = prec_elem_bytes(prec) * c->ld, wb = prec_elem_bytes(work_prec(prec)) * c->ld;
+    const size_t db = sizeof(double2) * c->ld, tb = M_MAX * M_MAX * sizeof(double2);
+    while ((int)w.lanes.size() < want) {
+        Lane L;
+        bool ok = dmalloc(c, &L.vring, 2 * m * fb) == DSBCG_OK && dmalloc(c, &L.zw, m * fb) == DSBCG_OK &&
+                  dmalloc(c, &L.y, m * fb) == DSBCG_OK && dmalloc(c, &L.P, m * wb) == DSBCG_OK &&
+                  dmalloc(c, &L.Xin, m * wb) == DSBCG_OK && dmalloc(c, (void**)&L.rhs, m * db) == DSBCG_OK &&
+                  dmalloc(c, (void**)&L.partials, gram_partial_doubles(M_MAX) * sizeof(double)) == DSBCG_OK &&
+                  dmalloc(c, (void**)&L.ss, small_state_bytes(1)) == DSBCG_OK &&
+                  dmalloc(c, (void**)&L.ctl, sizeof(Ctl)) == DSBCG_OK &&
+                  dmalloc(c, (void**)&L.G, M_MAX * M_MAX * sizeof(double2)) == DSBCG_OK &&
+                  dmalloc(c, (void**)&L.diag, M_MAX * sizeof(double)) == DSBCG_OK &&
+                  dmalloc(c, &L.coef_a, tb) == DSBCG_OK && dmalloc(c, &L.coef_bh, tb) == DSBCG_OK &&
+                  dmalloc(c, &L.coefS, tb) == DSBCG_OK && dmalloc(c, &L.coefU, tb) == DSBCG_OK &&
+                  dmalloc(c, &L.coefL, tb) == DSBCG_OK && dmalloc(c, (void**)&L.active, sizeof(int)) == DSBCG_OK &&
+                  dmalloc(c, (void**)&L.conv_step, m * sizeof(int)) == DSBCG_OK &&
+                  dmalloc(c, (void**)&L.res, m * sizeof(double)) == DSBCG_OK &&
+                  dmalloc(c, (void**)&L.sigma, sizeof(double)) == DSBCG_OK &&
+                  dmalloc(c, (void**)&L.target, m * sizeof(double)) == DSBCG_OK;
+        if (ok && cudaMallocHost((void**)&L.h_ctl, sizeof(Ctl)) == cudaSuccess) w.pinned.push_back(L.h_ctl);
+        else ok = false;
+        if (ok && cudaMallocHost((void**)&L.h_conv, m * sizeof(int)) == cudaSuccess) w.pinned.push_back(L.h_conv);
+        else ok = false;
+        if (ok && cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking) != cudaSuccess) {
+            L.st = nullptr;
+            ok = false;
+        }
+        if (ok && cudaEventCreateWithFlags(&L.ready, cudaEventDisableTiming) != cudaSuccess) {
+            L.ready = nullptr;
+            ok = false;
+        }
+        if (!ok) {
+            // out of memory (or streams): run with the lanes there are; what
+            // this attempt allocated stays in the workspace until it is freed
+            cudaGetLastError();
+            if (L.st) w.lanes.push_back(L);    // keeps the stream for free_ws; marked unusable below
+            break;
+        }
+        L.nblk = gram_blocks(c->n, m);
+        w.lanes.push_back(L);
+    }
+    int usable = 0;
+    for (auto& L : w.lanes) {
+        if (L.ready == nullptr && &L != &w.lanes[0]) break;
+        ++usable;
+    }
+    return std::min(usable, std::max(1, want));
 }
 
 // ---- profiling -------------------------------------------------------------
@@ -231,18 +351,20 @@ cudaEvent_t ev_get(dsbcg_ctx* c) {
 struct Prof {
     dsbcg_ctx* c;
     int cls;
+    cudaStream_t st;
     cudaEvent_t a = nullptr;
-    Prof(dsbcg_ctx* c_, int cls_, int nlaunch = 1) : c(c_), cls(cls_) {
+    Prof(dsbcg_ctx* c_, int cls_, int nlaunch = 1, cudaStream_t st_ = nullptr)
+        : c(c_), cls(cls_), st(st_ ? st_ : c_->st) {
         if (c->profiling) {
             a = ev_get(c);
-            cudaEventRecord(a, c->st);
+            cudaEventRecord(a, st);
         }
         c->klaunch[cls] += nlaunch;
     }
     ~Prof() {
         if (c->profiling) {
             cudaEvent_t b = ev_get(c);
-            cudaEventRecord(b, c->st);
+            cudaEventRecord(b, st);
             c->ev_live.push_back({cls, a, b});
         }
     }
@@ -325,108 +447,147 @@ struct InnerResult {
     bool converged = false;
 };
 
-// Joint inner solve on the right-hand sides `rhs` (m_in fields of precision
+// Inner solve on the right-hand sides `rhs` (m_in fields of precision
 // rhs_prec, field stride rhs_ld, internal layout: FP64 for FP64 storage, the
 // FP32 hi planes of double-float fields otherwise): for the shifts
-// sig[0..s_in), X_in[j] (work precision) receives the iterate, targets are
-// absolute residual norms per (j, i).
-dsbcg_status inner_solve(dsbcg_ctx* c, const void* rhs, int rhs_prec, size_t rhs_ld, int m_in, const double* sig,
-                         int s_in,
-                         const double* targets, int prec, double dtol, int max_steps, int freeze, int poll_every,
-                         InnerResult* out, int step_offset, int* conv_step_host) {
-    auto& w = c->ws;
+// sig[0..s_in), L.Xin[j] (work precision) receives the iterate, targets are
+// absolute residual norms per (j, i).  lane_start enqueues the
+// initialisation; lane_enqueue the next poll_every block steps and a copy of
+// the control block; lane_poll waits for them; lane_finish collects the
+// result.  All work of a lane runs on its stream.
+dsbcg_status lane_start(dsbcg_ctx* c, Lane& L, const void* rhs, int rhs_prec, size_t rhs_ld, int m_in,
+                        const double* sig, int s_in, const double* targets, int prec, double dtol, int max_steps,
+                        int freeze, int poll_every) {
     const int wp = work_prec(prec);
     const size_t ld = c->ld, n = c->n;
     const size_t fb = prec_elem_bytes(prec) * ld;
     const size_t wb = prec_elem_bytes(wp) * ld;
-    CK(cudaMemcpyAsync(w.sigma, sig, s_in * sizeof(double), cudaMemcpyHostToDevice, c->st));
-    CK(cudaMemcpyAsync(w.target, targets, (size_t)s_in * m_in * sizeof(double), cudaMemcpyHostToDevice, c->st));
-    CK(cudaMemsetAsync(w.conv_step, 0xff, (size_t)s_in * m_in * sizeof(int), c->st));
-    CK(cudaMemsetAsync(w.Xin, 0, (size_t)s_in * m_in * wb, c->st));
+    cudaStream_t st = L.st;
+    CK(cudaMemcpyAsync(L.sigma, sig, s_in * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(L.target, targets, (size_t)s_in * m_in * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(L.conv_step, 0xff, (size_t)s_in * m_in * sizeof(int), st));
+    CK(cudaMemsetAsync(L.Xin, 0, (size_t)s_in * m_in * wb, st));
     // a0: G0 = B^H B (in the right-hand sides' precision), pivoted Cholesky
     // with deflation, V_1 = B S0
     {
-        Prof p(c, DSBCG_KCLASS_GRAM);
-        launch_gram(rhs_prec, rhs, rhs, rhs_ld, n, nullptr, m_in, m_in, 1, 1, w.partials, w.nblk, 1.f, c->st);
+        Prof p(c, DSBCG_KCLASS_GRAM, 1, st);
+        launch_gram(rhs_prec, rhs, rhs, rhs_ld, n, nullptr, m_in, m_in, 1, 1, L.partials, L.nblk, 1.f, st);
     }
     {
-        Prof p(c, DSBCG_KCLASS_SMALL, 2);
-        launch_gram_reduce(w.partials, w.nblk, m_in, 1, 1, w.G, w.diag, nullptr, m_in, rhs_prec != P64, c->st);
-        launch_small_init(w.ss, w.ctl, w.G, w.diag, m_in, s_in, dtol, c->st);
+        Prof p(c, DSBCG_KCLASS_SMALL, 2, st);
+        launch_gram_reduce(L.partials, L.nblk, m_in, 1, 1, L.G, L.diag, nullptr, m_in, rhs_prec != P64, st);
+        launch_small_init(L.ss, L.ctl, L.G, L.diag, m_in, s_in, dtol, st);
     }
-    char* ring = (char*)w.vring;
+    char* ring = (char*)L.vring;
     {
-        Prof p(c, DSBCG_KCLASS_OTHER);
-        launch_init_basis(prec, ring + 1 * (size_t)m_in * fb, ld, rhs, rhs_prec, rhs_ld, n, small_state_S(w.ss),
-                          w.ctl, m_in, c->hscale, c->st);
+        Prof p(c, DSBCG_KCLASS_OTHER, 1, st);
+        launch_init_basis(prec, ring + 1 * (size_t)m_in * fb, ld, rhs, rhs_prec, rhs_ld, n, small_state_S(L.ss),
+                          L.ctl, m_in, c->hscale, st);
     }
     c->kbytes[DSBCG_KCLASS_GRAM] += (double)m_in * n * prec_elem_bytes(rhs_prec);
     c->kbytes[DSBCG_KCLASS_OTHER] += (double)m_in * n * (prec_elem_bytes(rhs_prec) + prec_elem_bytes(prec));
     CK(cudaGetLastError());
-    // block steps
-    int step = 0;
-    bool done = false;
-    while (!done) {
-        for (int q = 0; q < poll_every && step < max_steps; ++q) {
-            ++step;
-            void* Vk = ring + (size_t)(step % 2) * m_in * fb;
-            void* Vo = ring + (size_t)((step + 1) % 2) * m_in * fb;     // V_{k-1}, then V_{k+1}
-            {
-                Prof p(c, DSBCG_KCLASS_DSLASH);
-                launch_dslash(prec, w.zw, Vk, ld, c->links[prec], c->g, c->kappa, 0, 0, w.ctl, 0, m_in, c->hscale,
-                              c->st);
-            }
-            {
-                Prof p(c, DSBCG_KCLASS_DSLASH);
-                launch_dslash(prec, w.y, w.zw, ld, c->links[prec], c->g, c->kappa, 1, 1, w.ctl, 0, m_in,
-                              c->hscale, c->st);
-            }
-            {
-                Prof p(c, DSBCG_KCLASS_GRAM);
-                launch_gram(prec, Vk, w.y, ld, n, w.ctl, 0, m_in, 0, 1, w.partials, w.nblk, c->hscale, c->st);
-            }
-            {
-                Prof p(c, DSBCG_KCLASS_SMALL);
-                launch_small_alpha(w.ss, w.ctl, w.partials, w.nblk, m_in, wp, w.coef_a, w.coef_bh, c->st);
-            }
-            {
-                Prof p(c, DSBCG_KCLASS_UPDATE);
-                launch_block_update(prec, w.zw, w.y, Vk, Vo, ld, n, w.ctl, m_in, w.coef_a, w.coef_bh, c->hscale,
-                                    c->st);
-            }
-            {
-                Prof p(c, DSBCG_KCLASS_GRAM);
-                launch_gram(prec, w.zw, w.zw, ld, n, w.ctl, 0, m_in, 1, 0, w.partials, w.nblk, c->hscale, c->st);
-            }
-            {
-                Prof p(c, DSBCG_KCLASS_SMALL);
-                launch_small_step(w.ss, w.ctl, w.partials, w.nblk, s_in, m_in, dtol, w.sigma, w.target, freeze, wp,
-                                  w.coefS, w.coefU, w.coefL, w.active, w.conv_step, w.res, c->st);
-            }
-            {
-                Prof p(c, DSBCG_KCLASS_SHIFT);
-                launch_shift_update(prec, wp, Vo, w.zw, Vk, ld, w.P, w.Xin, ld, n, s_in, m_in, w.ctl, m_in, w.coefS,
-                                    w.coefU, w.coefL, w.active, c->hscale, c->st);
-            }
-            {
-                Prof p(c, DSBCG_KCLASS_SMALL);
-                launch_small_finish(w.ss, w.ctl, s_in, m_in, w.active, c->st);
-            }
+    L.m_in = m_in;
+    L.s_in = s_in;
+    L.prec = prec;
+    L.step = 0;
+    L.max_steps = max_steps;
+    L.freeze = freeze;
+    L.poll_every = poll_every;
+    L.dtol = dtol;
+    L.running = true;
+    return DSBCG_OK;
+}
+
+dsbcg_status lane_enqueue(dsbcg_ctx* c, Lane& L) {
+    const int prec = L.prec, wp = work_prec(prec), m_in = L.m_in, s_in = L.s_in;
+    const size_t ld = c->ld, n = c->n;
+    const size_t fb = prec_elem_bytes(prec) * ld;
+    cudaStream_t st = L.st;
+    char* ring = (char*)L.vring;
+    for (int q = 0; q < L.poll_every && L.step < L.max_steps; ++q) {
+        const int step = ++L.step;
+        void* Vk = ring + (size_t)(step % 2) * m_in * fb;
+        void* Vo = ring + (size_t)((step + 1) % 2) * m_in * fb;     // V_{k-1}, then V_{k+1}
+        {
+            Prof p(c, DSBCG_KCLASS_DSLASH, 1, st);
+            launch_dslash(prec, L.zw, Vk, ld, c->links[prec], c->g, c->kappa, 0, 0, L.ctl, 0, m_in, c->hscale, st);
         }
-        CK(cudaGetLastError());
-        CK(cudaMemcpyAsync(w.h_ctl, w.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->st));
-        CK(cudaStreamSynchronize(c->st));
-        prof_collect(c);
-        if (w.h_ctl->done || w.h_ctl->status != 0 || step >= max_steps) done = true;
+        {
+            Prof p(c, DSBCG_KCLASS_DSLASH, 1, st);
+            launch_dslash(prec, L.y, L.zw, ld, c->links[prec], c->g, c->kappa, 1, 1, L.ctl, 0, m_in, c->hscale, st);
+        }
+        {
+            Prof p(c, DSBCG_KCLASS_GRAM, 1, st);
+            launch_gram(prec, Vk, L.y, ld, n, L.ctl, 0, m_in, 0, 1, L.partials, L.nblk, c->hscale, st);
+        }
+        {
+            Prof p(c, DSBCG_KCLASS_SMALL, 1, st);
+            launch_small_alpha(L.ss, L.ctl, L.partials, L.nblk, m_in, wp, L.coef_a, L.coef_bh, st);
+        }
+        {
+            Prof p(c, DSBCG_KCLASS_UPDATE, 1, st);
+            launch_block_update(prec, L.zw, L.y, Vk, Vo, ld, n, L.ctl, m_in, L.coef_a, L.coef_bh, c->hscale, st);
+        }
+        {
+            Prof p(c, DSBCG_KCLASS_GRAM, 1, st);
+            launch_gram(prec, L.zw, L.zw, ld, n, L.ctl, 0, m_in, 1, 0, L.partials, L.nblk, c->hscale, st);
+        }
+        {
+            Prof p(c, DSBCG_KCLASS_SMALL, 1, st);
+            launch_small_step(L.ss, L.ctl, L.partials, L.nblk, s_in, m_in, L.dtol, L.sigma, L.target, L.freeze, wp,
+                              L.coefS, L.coefU, L.coefL, L.active, L.conv_step, L.res, st);
+        }
+        {
+            Prof p(c, DSBCG_KCLASS_SHIFT, 1, st);
+            launch_shift_update(prec, wp, Vo, L.zw, Vk, ld, L.P, L.Xin, ld, n, s_in, m_in, L.ctl, m_in, L.coefS,
+                                L.coefU, L.coefL, L.active, c->hscale, st);
+        }
+        {
+            Prof p(c, DSBCG_KCLASS_SMALL, 1, st);
+            launch_small_finish(L.ss, L.ctl, s_in, m_in, L.active, st);
+        }
     }
-    (void)wb;
-    CK(cudaMemcpyAsync(w.h_conv, w.conv_step, (size_t)s_in * m_in * sizeof(int), cudaMemcpyDeviceToHost, c->st));
-    CK(cudaStreamSynchronize(c->st));
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(L.h_ctl, L.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    return DSBCG_OK;
+}
+
+dsbcg_status lane_poll(dsbcg_ctx* c, Lane& L) {
+    (void)c;
+    CK(cudaStreamSynchronize(L.st));
+    if (L.h_ctl->done || L.h_ctl->status != 0 || L.step >= L.max_steps) L.running = false;
+    return DSBCG_OK;
+}
+
+// Run the started lanes to completion, enqueueing poll_every steps on each in
+// turn before waiting on any, so that their kernels overlap on the GPU.
+dsbcg_status run_lanes(dsbcg_ctx* c, Lane* const* lanes, int nl) {
+    for (;;) {
+        bool any = false;
+        for (int i = 0; i < nl; ++i)
+            if (lanes[i]->running) {
+                CKS(lane_enqueue(c, *lanes[i]));
+                any = true;
+            }
+        if (!any) break;
+        for (int i = 0; i < nl; ++i)
+            if (lanes[i]->running) CKS(lane_poll(c, *lanes[i]));
+        prof_collect(c);
+    }
+    return DSBCG_OK;
+}
+
+dsbcg_status lane_finish(dsbcg_ctx* c, Lane& L, InnerResult* out, int step_offset, int* conv_step_host) {
+    const int s_in = L.s_in, m_in = L.m_in, prec = L.prec, wp = work_prec(prec);
+    const size_t n = c->n;
+    CK(cudaMemcpyAsync(L.h_conv, L.conv_step, (size_t)s_in * m_in * sizeof(int), cudaMemcpyDeviceToHost, L.st));
+    CK(cudaStreamSynchronize(L.st));
     if (conv_step_host) {
         for (int t = 0; t < s_in * m_in; ++t)
-            conv_step_host[t] = w.h_conv[t] >= 0 ? w.h_conv[t] + step_offset : -1;
+            conv_step_host[t] = L.h_conv[t] >= 0 ? L.h_conv[t] + step_offset : -1;
     }
-    const Ctl& h = *w.h_ctl;
+    const Ctl& h = *L.h_ctl;
     {
         const double eb = (double)prec_elem_bytes(prec) * n, wbn = (double)prec_elem_bytes(wp) * n;
         const double links = 36.0 * c->V * (double)prec_elem_bytes(prec);
@@ -712,9 +873,11 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
         for (int j = 0; j < s; ++j)
             for (int i = 0; i < m; ++i) tg[(size_t)j * m + i] = std::max(drop * bn[i], 0.5 * tol * bn[i]);
         InnerResult ir;
-        CKS(inner_solve(c, w.B64, rprec, rld, m, sigma, s, tg.data(), prec, dtol, prm.max_block_steps,
-                        prm.freeze_converged,
-                        prm.poll_every, &ir, 0, conv.data()));
+        Lane* L0 = &w.lanes[0];
+        CKS(lane_start(c, *L0, w.B64, rprec, rld, m, sigma, s, tg.data(), prec, dtol, prm.max_block_steps,
+                       prm.freeze_converged, prm.poll_every));
+        CKS(run_lanes(c, &L0, 1));
+        CKS(lane_finish(c, *L0, &ir, 0, conv.data()));
         total_steps += ir.steps;
         mvms += ir.mvms;
         deflations += ir.deflations;
@@ -723,65 +886,100 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
         if (ir.status != 0) return DSBCG_ERR_CUDA;
         accumulate(w.X64, w.Xin, s * m);
     }
-    // --- high-precision true residuals and per-shift restarts.  Shift by shift: R_j of
-    // every column; while some column of shift j is above tol, restart on the
-    // unconverged columns of R_j, then recompute the residual of just those
-    // columns, which is the right-hand side of the next restart.
+    // --- high-precision true residuals and per-shift restarts.  Each shift
+    // has a list of unconverged columns (initially all).  In rounds of up to
+    // `nl` shifts: the true residual of each shift's listed columns; the
+    // columns still above tol are gathered as the right-hand sides of a
+    // restart of that shift (block CG on sigma_j I + A), and the restarts of
+    // the round run concurrently, one lane each; their solutions are added to
+    // X_j and the shift goes back into the queue for a new residual.  With
+    // profiling on, one lane (serial restarts, clean per-kernel timings).
+    const int nl = ensure_refine_lanes(c, (prm.refine && !c->profiling) ? std::min(s, 16) : 1);
     std::vector<double> r2(m);
-    std::vector<int> cols, pos(m);
+    std::vector<std::vector<int>> cols(s);
+    std::vector<char> full(s, 1);           // residual of all m columns still to be taken
+    std::deque<int> queue;
+    for (int j = 0; j < s; ++j) queue.push_back(j);
     auto gather = [&](double2* dst, const double2* src, const std::vector<int>& idx) -> dsbcg_status {
         for (size_t q = 0; q < idx.size(); ++q)
             CK(cudaMemcpyAsync(dst + q * ld, src + (size_t)idx[q] * ld, db, cudaMemcpyDeviceToDevice, c->st));
         return DSBCG_OK;
     };
-    for (int j = 0; j < s; ++j) {
-        double2* Xj = w.X64 + (size_t)j * m * ld;
-        CKS(true_residual(c, hp, w.R64, w.B64, Xj, m, sigma[j], r2.data()));
-        mvms += m;
-        cols.clear();
-        for (int i = 0; i < m; ++i) {
-            rel[(size_t)j * m + i] = bn[i] > 0 ? sqrt(r2[i]) / bn[i] : 0.0;
-            pos[i] = i;
-            if (rel[(size_t)j * m + i] > tol) cols.push_back(i);
-        }
-        while (!cols.empty() && prm.refine && restarts < prm.max_restarts && total_steps < prm.max_block_steps) {
-            const int mu = (int)cols.size();
-            std::vector<double> tg(mu);
-            std::vector<int> src(mu);
+    std::vector<int> round_j, round_lane;
+    std::vector<std::vector<double>> round_tg(nl);
+    while (!queue.empty()) {
+        round_j.clear();
+        while (!queue.empty() && (int)round_j.size() < nl) {
+            const int j = queue.front();
+            queue.pop_front();
+            double2* Xj = w.X64 + (size_t)j * m * ld;
+            // residual of the listed columns (all of them the first time)
+            std::vector<int>& cl = cols[j];
+            if (full[j]) {
+                cl.resize(m);
+                for (int i = 0; i < m; ++i) cl[i] = i;
+                CKS(true_residual(c, hp, w.R64, w.B64, Xj, m, sigma[j], r2.data()));
+                full[j] = 0;
+            } else {
+                CKS(gather(w.Xg, Xj, cl));
+                CKS(gather(w.Bg, w.B64, cl));
+                CKS(true_residual(c, hp, w.R64, w.Bg, w.Xg, (int)cl.size(), sigma[j], r2.data()));
+            }
+            mvms += (long long)cl.size();
+            std::vector<int> next, src;        // unconverged columns; their rows of R64
+            for (size_t q = 0; q < cl.size(); ++q) {
+                const int i = cl[q];
+                rel[(size_t)j * m + i] = bn[i] > 0 ? sqrt(r2[q]) / bn[i] : 0.0;
+                if (rel[(size_t)j * m + i] > tol) {
+                    next.push_back(i);
+                    src.push_back((int)q);
+                }
+            }
+            cl.swap(next);
+            if (cl.empty() || !prm.refine || restarts >= prm.max_restarts || total_steps >= prm.max_block_steps)
+                continue;
+            // restart of shift j on lane `li`
+            const int li = (int)round_j.size();
+            Lane& L = w.lanes[li];
+            const int mu = (int)cl.size();
+            std::vector<double>& tg = round_tg[li];
+            tg.resize(mu);
             for (int q = 0; q < mu; ++q) {
-                src[q] = pos[cols[q]];
-                const int i = cols[q];
+                const int i = cl[q];
                 tg[q] = std::max(drop * rel[(size_t)j * m + i] * bn[i], 0.5 * tol * bn[i]);
             }
-            CKS(gather(w.rhs, w.R64, src));
+            CKS(gather(L.rhs, w.R64, src));
+            if (L.st != c->st) {
+                CK(cudaEventRecord(L.ready, c->st));
+                CK(cudaStreamWaitEvent(L.st, L.ready, 0));
+            }
+            CKS(lane_start(c, L, L.rhs, rprec, rld, mu, &sigma[j], 1, tg.data(), prec, dtol,
+                           std::max(1, prm.max_block_steps - total_steps), prm.freeze_converged, prm.poll_every));
+            restarts += 1;
+            round_j.push_back(j);
+        }
+        if (round_j.empty()) continue;
+        std::vector<Lane*> lp;
+        for (size_t li = 0; li < round_j.size(); ++li) lp.push_back(&w.lanes[li]);
+        CKS(run_lanes(c, lp.data(), (int)lp.size()));
+        const int step0 = total_steps;
+        for (size_t li = 0; li < round_j.size(); ++li) {
+            const int j = round_j[li];
+            Lane& L = w.lanes[li];
             InnerResult ir;
-            CKS(inner_solve(c, w.rhs, rprec, rld, mu, &sigma[j], 1, tg.data(), prec, dtol,
-                            std::max(1, prm.max_block_steps - total_steps), prm.freeze_converged, prm.poll_every,
-                            &ir, total_steps, conv_tmp.data()));
+            CKS(lane_finish(c, L, &ir, step0, conv_tmp.data()));
             total_steps += ir.steps;
             mvms += ir.mvms;
             deflations += ir.deflations;
-            restarts += 1;
             if (ir.status == DSBCG_ERR_NOT_HPD) return DSBCG_ERR_NOT_HPD;
             if (ir.status != 0) return DSBCG_ERR_CUDA;
-            for (int q = 0; q < mu; ++q) {
-                if (conv_tmp[q] >= 0) conv[(size_t)j * m + cols[q]] = conv_tmp[q];
-                accumulate(Xj + (size_t)cols[q] * ld,
-                           (char*)w.Xin + (size_t)q * ld * prec_elem_bytes(work_prec(prec)), 1);
+            double2* Xj = w.X64 + (size_t)j * m * ld;
+            for (size_t q = 0; q < cols[j].size(); ++q) {
+                if (conv_tmp[q] >= 0) conv[(size_t)j * m + cols[j][q]] = conv_tmp[q];
+                accumulate(Xj + (size_t)cols[j][q] * ld,
+                           (char*)L.Xin + q * ld * prec_elem_bytes(work_prec(prec)), 1);
             }
-            // residual of the restarted columns only
-            CKS(gather(w.Xg, Xj, cols));
-            CKS(gather(w.Bg, w.B64, cols));
-            CKS(true_residual(c, hp, w.R64, w.Bg, w.Xg, mu, sigma[j], r2.data()));
-            mvms += mu;
-            std::vector<int> next;
-            for (int q = 0; q < mu; ++q) {
-                const int i = cols[q];
-                rel[(size_t)j * m + i] = bn[i] > 0 ? sqrt(r2[q]) / bn[i] : 0.0;
-                pos[i] = q;
-                if (rel[(size_t)j * m + i] > tol) next.push_back(i);
-            }
-            cols.swap(next);
+            queue.push_back(j);           // its new residual decides the next restart
         }
     }
     for (double r : rel)

@@ -160,3 +160,20 @@ def test_w2_full_size_mixed(w2):
         # the library's double-float true residual agrees with the oracle's
         # FP64 recomputation far below tol
         assert abs(rel - st["true_relres"][j, i]) <= 1e-2 * wl["tol"], (j, i, rel, st["true_relres"][j, i])
+
+
+def test_concurrent_restarts_match_serial(w1):
+    """The per-shift restarts run concurrently on separate streams; with the
+    library's profiling on they run one after another.  Each restart only
+    touches its own lane's buffers, so X is bitwise the same either way."""
+    wl, Ad, Xd, ctx = w1
+    B = torch.from_numpy(wl["B"]).to(DEV)
+    Xc, stc = ctx.solve(B, wl["sigma"], 1e-10, storage="fp32")
+    ctx.set_profiling(True)
+    Xs, sts = ctx.solve(B, wl["sigma"], 1e-10, storage="fp32")
+    ctx.set_profiling(False)
+    assert stc["code"] == 0 and sts["code"] == 0
+    assert stc["restarts"] == sts["restarts"] >= len(wl["sigma"])
+    assert stc["block_steps"] == sts["block_steps"]
+    assert torch.equal(Xc, Xs)
+    assert np.array_equal(stc["true_relres"], sts["true_relres"])
