@@ -369,16 +369,24 @@ struct Prof {
         }
     }
 };
+// Add the durations of completed launch-event pairs to their classes; pairs
+// whose stream has not reached them yet stay for a later call.
 void prof_collect(dsbcg_ctx* c) {
-    // caller has synchronised the stream
+    std::vector<KEvent> pending;
     for (auto& k : c->ev_live) {
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, k.a, k.b);
-        c->kms[k.cls] += ms;
+        const cudaError_t e = cudaEventElapsedTime(&ms, k.a, k.b);
+        if (e == cudaErrorNotReady) {
+            cudaGetLastError();
+            pending.push_back(k);
+            continue;
+        }
+        if (e == cudaSuccess) c->kms[k.cls] += ms;
+        else cudaGetLastError();
         c->ev_pool.push_back(k.a);
         c->ev_pool.push_back(k.b);
     }
-    c->ev_live.clear();
+    c->ev_live.swap(pending);
 }
 
 // ---- high-precision operator and true residual ------------------------------
@@ -887,33 +895,47 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
         accumulate(w.X64, w.Xin, s * m);
     }
     // --- high-precision true residuals and per-shift restarts.  Each shift
-    // has a list of unconverged columns (initially all).  In rounds of up to
-    // `nl` shifts: the true residual of each shift's listed columns; the
-    // columns still above tol are gathered as the right-hand sides of a
-    // restart of that shift (block CG on sigma_j I + A), and the restarts of
-    // the round run concurrently, one lane each; their solutions are added to
-    // X_j and the shift goes back into the queue for a new residual.  With
-    // profiling on, one lane (serial restarts, clean per-kernel timings).
-    const int nl = ensure_refine_lanes(c, (prm.refine && !c->profiling) ? std::min(s, 16) : 1);
+    // has a list of unconverged columns (initially all) and waits in a queue
+    // for its true residual, taken on the context's stream.  Columns still
+    // above tol become the right-hand sides of a restart of that shift (block
+    // CG on sigma_j I + A) on a free lane; lanes run concurrently on their
+    // own streams, and a finished restart's solution is added to X_j and the
+    // shift queued again, so residuals overlap the restarts still running.
+    // With profiling on, lane 0 alone on the context's stream (serial
+    // restarts, clean per-kernel timings); results are bitwise the same.
+    int lane_lo = 0, lane_hi = 1;                      // refinement lanes [lane_lo, lane_hi)
+    if (prm.refine && !c->profiling && s > 1) {
+        const int got = ensure_refine_lanes(c, 1 + std::min(s, 16));
+        if (got > 1) {
+            lane_lo = 1;
+            lane_hi = got;
+        }
+    }
     std::vector<double> r2(m);
     std::vector<std::vector<int>> cols(s);
     std::vector<char> full(s, 1);           // residual of all m columns still to be taken
     std::deque<int> queue;
     for (int j = 0; j < s; ++j) queue.push_back(j);
+    std::vector<int> lane_j(w.lanes.size(), -1);       // shift restarted on each lane
+    std::vector<std::vector<double>> lane_tg(w.lanes.size());
     auto gather = [&](double2* dst, const double2* src, const std::vector<int>& idx) -> dsbcg_status {
         for (size_t q = 0; q < idx.size(); ++q)
             CK(cudaMemcpyAsync(dst + q * ld, src + (size_t)idx[q] * ld, db, cudaMemcpyDeviceToDevice, c->st));
         return DSBCG_OK;
     };
-    std::vector<int> round_j, round_lane;
-    std::vector<std::vector<double>> round_tg(nl);
-    while (!queue.empty()) {
-        round_j.clear();
-        while (!queue.empty() && (int)round_j.size() < nl) {
+    // residuals of queued shifts while a lane is free; restarts where needed
+    auto feed = [&]() -> dsbcg_status {
+        for (;;) {
+            int li = -1;
+            for (int l = lane_lo; l < lane_hi; ++l)
+                if (lane_j[l] < 0) {
+                    li = l;
+                    break;
+                }
+            if (li < 0 || queue.empty()) return DSBCG_OK;
             const int j = queue.front();
             queue.pop_front();
             double2* Xj = w.X64 + (size_t)j * m * ld;
-            // residual of the listed columns (all of them the first time)
             std::vector<int>& cl = cols[j];
             if (full[j]) {
                 cl.resize(m);
@@ -938,11 +960,9 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
             cl.swap(next);
             if (cl.empty() || !prm.refine || restarts >= prm.max_restarts || total_steps >= prm.max_block_steps)
                 continue;
-            // restart of shift j on lane `li`
-            const int li = (int)round_j.size();
             Lane& L = w.lanes[li];
             const int mu = (int)cl.size();
-            std::vector<double>& tg = round_tg[li];
+            std::vector<double>& tg = lane_tg[li];
             tg.resize(mu);
             for (int q = 0; q < mu; ++q) {
                 const int i = cl[q];
@@ -955,19 +975,31 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
             }
             CKS(lane_start(c, L, L.rhs, rprec, rld, mu, &sigma[j], 1, tg.data(), prec, dtol,
                            std::max(1, prm.max_block_steps - total_steps), prm.freeze_converged, prm.poll_every));
+            CKS(lane_enqueue(c, L));
             restarts += 1;
-            round_j.push_back(j);
+            lane_j[li] = j;
         }
-        if (round_j.empty()) continue;
-        std::vector<Lane*> lp;
-        for (size_t li = 0; li < round_j.size(); ++li) lp.push_back(&w.lanes[li]);
-        CKS(run_lanes(c, lp.data(), (int)lp.size()));
-        const int step0 = total_steps;
-        for (size_t li = 0; li < round_j.size(); ++li) {
-            const int j = round_j[li];
-            Lane& L = w.lanes[li];
+    };
+    CKS(feed());
+    for (;;) {
+        bool busy = false;
+        for (int l = lane_lo; l < lane_hi; ++l)
+            if (lane_j[l] >= 0) busy = true;
+        if (!busy) break;
+        for (int l = lane_lo; l < lane_hi; ++l)
+            if (lane_j[l] >= 0) CKS(lane_poll(c, w.lanes[l]));
+        prof_collect(c);
+        for (int l = lane_lo; l < lane_hi; ++l) {
+            if (lane_j[l] < 0) continue;
+            Lane& L = w.lanes[l];
+            if (L.running) {
+                CKS(lane_enqueue(c, L));
+                continue;
+            }
+            // restart finished: fold its solution into X_j
+            const int j = lane_j[l];
             InnerResult ir;
-            CKS(lane_finish(c, L, &ir, step0, conv_tmp.data()));
+            CKS(lane_finish(c, L, &ir, total_steps, conv_tmp.data()));
             total_steps += ir.steps;
             mvms += ir.mvms;
             deflations += ir.deflations;
@@ -979,8 +1011,10 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
                 accumulate(Xj + (size_t)cols[j][q] * ld,
                            (char*)L.Xin + q * ld * prec_elem_bytes(work_prec(prec)), 1);
             }
+            lane_j[l] = -1;
             queue.push_back(j);           // its new residual decides the next restart
         }
+        CKS(feed());
     }
     for (double r : rel)
         if (!(r <= tol)) result = DSBCG_NOT_CONVERGED;
