@@ -230,15 +230,21 @@ __global__ void __launch_bounds__(256) init_basis_kernel(typename Tr<P>::S2* __r
                                                          const Ctl* __restrict__ ctl, int nf_in, float hscale) {
     // the product is formed in the arithmetic precision of the storage: FP64
     // for FP64 fields, FP32 otherwise (the result is stored in FP32 or less);
-    // S is converted once per CTA (FP64 -> FP32 conversion runs at the FP64
-    // rate on GB300)
+    // S is read once per CTA
     using R = typename Tr<P>::R;
     using C = typename Tr<P>::C;
     const int m1 = ctl->mk;
     __shared__ C ss[NF * NF];
     for (int t = threadIdx.x; t < NF * NF; t += blockDim.x) {
-        const double2 v = S[(t / NF) * M_MAX + (t % NF)];
-        ss[t] = mk(R(v.x), R(v.y));
+        if constexpr (P == P64) {
+            const double2 v = S[(t / NF) * M_MAX + (t % NF)];
+            ss[t] = mk(R(v.x), R(v.y));
+        } else {
+            // reduced storage: the m x m state is double-float
+            // (re.hi, re.lo, im.hi, im.lo); its hi words are the FP32 values
+            const float4 v = reinterpret_cast<const float4*>(S)[(t / NF) * M_MAX + (t % NF)];
+            ss[t] = mk(R(v.x), R(v.z));
+        }
     }
     __syncthreads();
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;

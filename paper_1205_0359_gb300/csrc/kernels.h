@@ -80,10 +80,10 @@ void launch_shift_update(int prec, int wprec, void* Vnext, const void* W, const 
                          const void* coefL, const int* active, float hscale, cudaStream_t st);
 
 // ---- small.cu ---------------------------------------------------------------
-struct SmallState;     // device FP64 m x m state, defined in small.cu
+struct SmallState;     // device m x m state (FP64 or double-float), defined in small.cu
 size_t small_state_bytes(int s);
-void launch_small_init(SmallState* ss, Ctl* ctl, const double2* G0, const double* ref, int m,
-                       int s, double dtol, cudaStream_t st);
+void launch_small_init(SmallState* ss, Ctl* ctl, const double2* G0, const double* ref, int m, int s, double dtol,
+                       int wprec, cudaStream_t st);
 // alpha_k from the Gram partials of V_k^H Y (+ coefficient tiles for the block update)
 void launch_small_alpha(SmallState* ss, const Ctl* ctl, const double* partials, int nblk, int nf_max,
                         int wprec, void* coef_a, void* coef_bh, cudaStream_t st);

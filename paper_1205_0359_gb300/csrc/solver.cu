@@ -484,7 +484,7 @@ dsbcg_status lane_start(dsbcg_ctx* c, Lane& L, const void* rhs, int rhs_prec, si
     {
         Prof p(c, DSBCG_KCLASS_SMALL, 2, st);
         launch_gram_reduce(L.partials, L.nblk, m_in, 1, 1, L.G, L.diag, nullptr, m_in, rhs_prec != P64, st);
-        launch_small_init(L.ss, L.ctl, L.G, L.diag, m_in, s_in, dtol, st);
+        launch_small_init(L.ss, L.ctl, L.G, L.diag, m_in, s_in, dtol, wp, st);
     }
     char* ring = (char*)L.vring;
     {
