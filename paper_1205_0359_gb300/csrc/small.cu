@@ -74,7 +74,7 @@ const double2* small_state_S(const SmallState* ss) { return ss->sh.S; }
 namespace {
 
 constexpr int WS = 32;             // the pivoted QR runs on one warp
-constexpr int NT = 256;            // threads of the CTAs that also reduce partial sums
+constexpr int NT = 1024;           // threads of the CTAs that also reduce partial sums
 constexpr int GSL = 36;            // slots per 4 x 4 tile in the Gram partials
 constexpr int RED_MAX = 1024;      // group sums held in shared memory by reduce_partials
 
@@ -385,7 +385,8 @@ __device__ __forceinline__ void reduce_store(T* G, int ld, typename Sc<T>::R* di
 // additions, the chains combined in double-float.  Consecutive threads take
 // consecutive slots (coalesced rows of 36); when the CTA has threads to spare,
 // ng groups split the CTAs' range and their sums are added in group order;
-// four interleaved accumulators per thread keep several loads in flight.
+// RC interleaved accumulators per thread keep several loads in flight (the
+// partials come from L2, so the sum is latency-bound).
 // Fixed order: bitwise reproducible.
 template <class T>
 __device__ void reduce_partials(const double* __restrict__ part, int nblk, int nf_max, int herm, T* G, int ld,
@@ -403,37 +404,49 @@ __device__ void reduce_partials(const double* __restrict__ part, int nblk, int n
         const int b0 = grp * chunk, b1 = min(nblk, b0 + chunk);
         const int tile = it / GSL, q = it % GSL;
         const size_t off = (size_t)tile * nblk * GSL + q;
+        constexpr int RC = 8;
         R s;
         if constexpr (is_fp64<T>()) {
             const double* p = part + off;
-            double a[4] = {0.0, 0.0, 0.0, 0.0};
-            int b = b0;
-            for (; b + 4 <= b1; b += 4)
+            double a[RC];
 #pragma unroll
-                for (int r = 0; r < 4; ++r) a[r] += p[(size_t)(b + r) * GSL];
+            for (int r = 0; r < RC; ++r) a[r] = 0.0;
+            int b = b0;
+            for (; b + RC <= b1; b += RC)
+#pragma unroll
+                for (int r = 0; r < RC; ++r) a[r] += p[(size_t)(b + r) * GSL];
             for (; b < b1; ++b) a[0] += p[(size_t)b * GSL];
-            s = (a[0] + a[1]) + (a[2] + a[3]);
+            double t = 0.0;
+#pragma unroll
+            for (int r = 0; r < RC; ++r) t += a[r];
+            s = t;
         } else {
             const float* p = reinterpret_cast<const float*>(part) + off;
-            float sum[4] = {0.f, 0.f, 0.f, 0.f}, comp[4] = {0.f, 0.f, 0.f, 0.f};
-            int b = b0;
-            for (; b + 4 <= b1; b += 4) {
+            float sum[RC], comp[RC];
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const float y = p[(size_t)(b + r) * GSL] - comp[r];
-                    const float t = sum[r] + y;
-                    comp[r] = (t - sum[r]) - y;
+            for (int r = 0; r < RC; ++r) sum[r] = comp[r] = 0.f;
+            int b = b0;
+            for (; b + RC <= b1; b += RC) {
+                float y[RC];
+#pragma unroll
+                for (int r = 0; r < RC; ++r) y[r] = p[(size_t)(b + r) * GSL];
+#pragma unroll
+                for (int r = 0; r < RC; ++r) {
+                    const float yy = y[r] - comp[r];
+                    const float t = sum[r] + yy;
+                    comp[r] = (t - sum[r]) - yy;
                     sum[r] = t;
                 }
             }
             for (; b < b1; ++b) {
-                const float y = p[(size_t)b * GSL] - comp[0];
-                const float t = sum[0] + y;
-                comp[0] = (t - sum[0]) - y;
+                const float yy = p[(size_t)b * GSL] - comp[0];
+                const float t = sum[0] + yy;
+                comp[0] = (t - sum[0]) - yy;
                 sum[0] = t;
             }
-            s = S::add(S::add(S::kahan(sum[0], comp[0]), S::kahan(sum[1], comp[1])),
-                       S::add(S::kahan(sum[2], comp[2]), S::kahan(sum[3], comp[3])));
+            s = S::kahan(sum[0], comp[0]);
+#pragma unroll
+            for (int r = 1; r < RC; ++r) s = S::add(s, S::kahan(sum[r], comp[r]));
         }
         if (ng > 1) red[grp * items + it] = s;
         else reduce_store<T>(G, ld, diag, Tt, herm, nf_max, it, s);
@@ -719,10 +732,10 @@ void launch_small_init(SmallState* ss, Ctl* ctl, const double2* G0, const double
 void launch_small_alpha(SmallState* ss, const Ctl* ctl, const double* partials, int nblk, int nf_max, int wprec,
                         void* coef_a, void* coef_bh, cudaStream_t st) {
     if (wprec == P64)
-        small_alpha_kernel<double2><<<1, 256, 0, st>>>(as_state<double2>(ss), ctl, partials, nblk, nf_max, wprec,
+        small_alpha_kernel<double2><<<1, NT, 0, st>>>(as_state<double2>(ss), ctl, partials, nblk, nf_max, wprec,
                                                        coef_a, coef_bh);
     else
-        small_alpha_kernel<ddc><<<1, 256, 0, st>>>(as_state<ddc>(ss), ctl, partials, nblk, nf_max, wprec, coef_a,
+        small_alpha_kernel<ddc><<<1, NT, 0, st>>>(as_state<ddc>(ss), ctl, partials, nblk, nf_max, wprec, coef_a,
                                                    coef_bh);
 }
 
