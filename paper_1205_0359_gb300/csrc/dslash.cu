@@ -215,7 +215,7 @@ __device__ __forceinline__ void su3_mul(const typename Tr<P>::S2* __restrict__ u
 }
 
 template <int P>
-__global__ void __launch_bounds__(32, P == PDD ? 12 : 16) dslash_kernel(typename Tr<P>::S2* __restrict__ out,
+__global__ void __launch_bounds__(32, (P == PDD || P == P64) ? 12 : 24) dslash_kernel(typename Tr<P>::S2* __restrict__ out,
                                                    const typename Tr<P>::S2* __restrict__ in,
                                                    size_t ld, const typename Tr<P>::S2* __restrict__ links,
                                                    Geom g, typename Tr<P>::R kappa, int g5in, int g5out,
