@@ -894,6 +894,17 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
         if (ir.status != 0) return DSBCG_ERR_CUDA;
         accumulate(w.X64, w.Xin, s * m);
     }
+    // --- output of a finished shift: its X_j goes to the caller's buffer as
+    // soon as its last true residual is in (device or mapped pinned host
+    // memory; other host memory is staged at the end), so that the transfer
+    // overlaps the restarts of the other shifts
+    void* const xmap = x_dev ? nullptr : mapped_host_ptr(X);
+    double2* const xout = x_dev ? (double2*)X : (double2*)xmap;
+    auto emit = [&](int j) {
+        if (!xout) return;
+        Prof p(c, DSBCG_KCLASS_OTHER);
+        unpack_any(c, hp, xout + (size_t)j * m * n, w.X64 + (size_t)j * m * ld, m);
+    };
     // --- high-precision true residuals and per-shift restarts.  Each shift
     // has a list of unconverged columns (initially all) and waits in a queue
     // for its true residual, taken on the context's stream.  Columns still
@@ -958,8 +969,10 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
                 }
             }
             cl.swap(next);
-            if (cl.empty() || !prm.refine || restarts >= prm.max_restarts || total_steps >= prm.max_block_steps)
+            if (cl.empty() || !prm.refine || restarts >= prm.max_restarts || total_steps >= prm.max_block_steps) {
+                emit(j);                        // X_j is final
                 continue;
+            }
             Lane& L = w.lanes[li];
             const int mu = (int)cl.size();
             std::vector<double>& tg = lane_tg[li];
@@ -1019,21 +1032,13 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
     for (double r : rel)
         if (!(r <= tol)) result = DSBCG_NOT_CONVERGED;
 
-    // --- output X (canonical complex128 [s][m][n])
+    // --- output X (canonical complex128 [s][m][n]): device and mapped pinned
+    // host buffers were written shift by shift above
     auto unpack = [&](double2* dst, const double2* src, int nf) {
         Prof p(c, DSBCG_KCLASS_OTHER);
         unpack_any(c, hp, dst, src, nf);
     };
-    double2* xcanon = nullptr;
-    if (x_dev) {
-        xcanon = (double2*)X;
-        unpack(xcanon, w.X64, s * m);
-        CK(cudaGetLastError());
-        CK(cudaStreamSynchronize(c->st));
-    } else if (void* xmap = mapped_host_ptr(X)) {
-        // pinned host memory mapped into the device address space: the
-        // unpack kernel writes the canonical layout straight into it
-        unpack((double2*)xmap, w.X64, s * m);
+    if (xout) {
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(c->st));
     } else {
