@@ -51,10 +51,10 @@ typedef enum {
 } dsbcg_status;
 
 /* Storage precision of spinor fields and links inside the Krylov iteration.
- * Arithmetic on FP32/BF16/FP16 storage is FP32; the m x m block coefficients,
- * deflation and per-shift recurrences are always FP64.  True residuals and
- * accumulated solutions are FP64 for FP64 storage and double-float for the
- * reduced storages.
+ * Arithmetic on FP32/BF16/FP16 storage is FP32.  The m x m block
+ * coefficients, deflation, per-shift recurrences, true residuals and
+ * accumulated solutions are FP64 for FP64 storage; for the reduced storages
+ * they are double-float by default and FP64 with dsbcg_params.fp64_residuals.
  * DSBCG_PREC_DF32 ("double-float"): each real number is an unevaluated sum
  * hi + lo of two FP32 words (48-bit significand, FP32 exponent range,
  * arithmetic on the FP32 pipes through error-free transformations).  It is
@@ -88,6 +88,10 @@ typedef struct {
     int freeze_converged;   /* stop updating converged (i, j) systems (Sec. 4) */
     int refine;             /* 1: after the joint solve, restart each unconverged shift
                                separately (block CG) until its true residual meets tol */
+    int fp64_residuals;     /* reduced storages only.  0 (default): true residuals,
+                               accumulated solutions and the m x m coefficient work in
+                               double-float arithmetic (DSBCG_PREC_DF32) on the FP32
+                               pipes; 1: all of them in IEEE FP64, as with FP64 storage */
 } dsbcg_params;
 
 typedef struct {
@@ -139,8 +143,9 @@ dsbcg_status dsbcg_update_gauge(dsbcg_ctx* ctx, const void* gauge);
  * factorisation of sigma_j I + T per shift; directions that become linearly
  * dependent are deflated (Sec. 1, Sec. 3).  With FP32/BF16/FP16 storage the
  * Krylov iteration runs in reduced precision inside a loop that recomputes
- * true residuals in double-float arithmetic (DSBCG_PREC_DF32) and restarts
- * (reliable updates); with FP64 storage residuals are FP64.  A double-float
+ * true residuals in double-float arithmetic (DSBCG_PREC_DF32; FP64 with
+ * params->fp64_residuals) and restarts (reliable updates); with FP64
+ * storage residuals are FP64.  A double-float
  * residual carries an absolute error of roughly 2^-44 |A| |x|, so it
  * certifies tol down to about 1e-13 times the condition number of
  * sigma_j I + A.

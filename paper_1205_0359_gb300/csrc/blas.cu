@@ -58,7 +58,7 @@ void launch_gram_reduce(const double* partials, int nblk, int nf_max, int herm, 
 #define EXTERN_P(P)                                                                                      \
     extern template void launch_bu_t<P>(void*, const void*, const void*, const void*, size_t, size_t, const Ctl*, \
                                         int, const void*, const void*, float, cudaStream_t);                 \
-    extern template void launch_ib_t<P>(void*, size_t, const void*, int, size_t, size_t, const double2*,      \
+    extern template void launch_ib_t<P>(void*, size_t, const void*, int, size_t, size_t, const double2*, int, \
                                         const Ctl*, int, float, cudaStream_t);                               \
     extern template void launch_su_t<P>(void*, const void*, const void*, size_t, void*, void*, size_t, size_t,  \
                                         int, int, Ctl*, int, const void*, const void*, const void*,           \
@@ -83,12 +83,12 @@ void launch_block_update(int prec, void* W, const void* Y, const void* Vk, const
 }
 
 void launch_init_basis(int prec, void* V1, size_t ldv, const void* B, int bprec, size_t ldb, size_t n,
-                       const double2* S, const Ctl* ctl, int nf_in, float hscale, cudaStream_t st) {
+                       const double2* S, int s_dd, const Ctl* ctl, int nf_in, float hscale, cudaStream_t st) {
     switch (prec) {
-        case P64: launch_ib_t<P64>(V1, ldv, B, bprec, ldb, n, S, ctl, nf_in, hscale, st); break;
-        case P32: launch_ib_t<P32>(V1, ldv, B, bprec, ldb, n, S, ctl, nf_in, hscale, st); break;
-        case PBF16: launch_ib_t<PBF16>(V1, ldv, B, bprec, ldb, n, S, ctl, nf_in, hscale, st); break;
-        case PF16: launch_ib_t<PF16>(V1, ldv, B, bprec, ldb, n, S, ctl, nf_in, hscale, st); break;
+        case P64: launch_ib_t<P64>(V1, ldv, B, bprec, ldb, n, S, s_dd, ctl, nf_in, hscale, st); break;
+        case P32: launch_ib_t<P32>(V1, ldv, B, bprec, ldb, n, S, s_dd, ctl, nf_in, hscale, st); break;
+        case PBF16: launch_ib_t<PBF16>(V1, ldv, B, bprec, ldb, n, S, s_dd, ctl, nf_in, hscale, st); break;
+        case PF16: launch_ib_t<PF16>(V1, ldv, B, bprec, ldb, n, S, s_dd, ctl, nf_in, hscale, st); break;
     }
 }
 

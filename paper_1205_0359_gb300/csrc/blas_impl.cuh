@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(256) block_update_kernel(typename Tr<P>::S2* _
 template <int P, int NF, int PIN>
 __global__ void __launch_bounds__(256) init_basis_kernel(typename Tr<P>::S2* __restrict__ V1, size_t ldv,
                                                          const typename Tr<PIN>::S2* __restrict__ B, size_t ldb,
-                                                         size_t n, const double2* __restrict__ S,
+                                                         size_t n, const double2* __restrict__ S, int s_dd,
                                                          const Ctl* __restrict__ ctl, int nf_in, float hscale) {
     // the product is formed in the arithmetic precision of the storage: FP64
     // for FP64 fields, FP32 otherwise (the result is stored in FP32 or less);
@@ -236,12 +236,12 @@ __global__ void __launch_bounds__(256) init_basis_kernel(typename Tr<P>::S2* __r
     const int m1 = ctl->mk;
     __shared__ C ss[NF * NF];
     for (int t = threadIdx.x; t < NF * NF; t += blockDim.x) {
-        if constexpr (P == P64) {
+        if (!s_dd) {
             const double2 v = S[(t / NF) * M_MAX + (t % NF)];
             ss[t] = mk(R(v.x), R(v.y));
         } else {
-            // reduced storage: the m x m state is double-float
-            // (re.hi, re.lo, im.hi, im.lo); its hi words are the FP32 values
+            // double-float m x m state (re.hi, re.lo, im.hi, im.lo): the hi
+            // words are the FP32 values (reduced storage only)
             const float4 v = reinterpret_cast<const float4*>(S)[(t / NF) * M_MAX + (t % NF)];
             ss[t] = mk(R(v.x), R(v.z));
         }
@@ -749,19 +749,21 @@ void launch_bu_t(void* W, const void* Y, const void* Vk, const void* Vp, size_t 
 }
 
 template <int P>
-void launch_ib_t(void* V1, size_t ldv, const void* B, int bprec, size_t ldb, size_t n, const double2* S,
+void launch_ib_t(void* V1, size_t ldv, const void* B, int bprec, size_t ldb, size_t n, const double2* S, int s_dd,
                  const Ctl* ctl, int nf_in, float hscale, cudaStream_t st) {
     using S2 = typename Tr<P>::S2;
     int g = (int)((n + 255) / 256);
     if (bprec == P64 || P == P64) {
         // FP64 storage always starts from FP64 right-hand sides
 #define BI_IB(NF) \
-    init_basis_kernel<P, NF, P64><<<g, 256, 0, st>>>((S2*)V1, ldv, (const double2*)B, ldb, n, S, ctl, nf_in, hscale)
+    init_basis_kernel<P, NF, P64><<<g, 256, 0, st>>>((S2*)V1, ldv, (const double2*)B, ldb, n, S, s_dd, ctl, nf_in, \
+                                                     hscale)
         BI_DISPATCH_NF(nf_in, BI_IB)
 #undef BI_IB
     } else {
 #define BI_IB(NF) \
-    init_basis_kernel<P, NF, P32><<<g, 256, 0, st>>>((S2*)V1, ldv, (const float2*)B, ldb, n, S, ctl, nf_in, hscale)
+    init_basis_kernel<P, NF, P32><<<g, 256, 0, st>>>((S2*)V1, ldv, (const float2*)B, ldb, n, S, s_dd, ctl, nf_in, \
+                                                     hscale)
         BI_DISPATCH_NF(nf_in, BI_IB)
 #undef BI_IB
     }
@@ -799,8 +801,8 @@ void launch_su_t(void* Vnext, const void* W, const void* Vk, size_t ld, void* Pp
 #define BI_INSTANTIATE(P)                                                                                  \
     template void launch_bu_t<P>(void*, const void*, const void*, const void*, size_t, size_t, const Ctl*, int, \
                                  const void*, const void*, float, cudaStream_t);                          \
-    template void launch_ib_t<P>(void*, size_t, const void*, int, size_t, size_t, const double2*, const Ctl*, \
-                                 int, float, cudaStream_t);                                                \
+    template void launch_ib_t<P>(void*, size_t, const void*, int, size_t, size_t, const double2*, int,       \
+                                 const Ctl*, int, float, cudaStream_t);                                    \
     template void launch_su_t<P>(void*, const void*, const void*, size_t, void*, void*, size_t, size_t, int, int, \
                                  Ctl*, int, const void*, const void*, const void*, const int*, float,         \
                                  cudaStream_t);

@@ -68,9 +68,10 @@ void launch_block_update(int prec, void* W, const void* Y, const void* Vk, const
                          size_t ld, size_t n, const Ctl* ctl, int nf_max,
                          const void* coef_a, const void* coef_bh, float hscale, cudaStream_t st);
 // V1 = B S (B in precision bprec: FP64, or FP32 for reduced storage;
-// storage-precision V1), S from device (FP64, M_MAX x M_MAX)
+// storage-precision V1), S from the device m x m state (M_MAX x M_MAX, FP64,
+// or double-float when s_dd)
 void launch_init_basis(int prec, void* V1, size_t ldv, const void* B, int bprec, size_t ldb, size_t n,
-                       const double2* S, const Ctl* ctl, int nf_in, float hscale, cudaStream_t st);
+                       const double2* S, int s_dd, const Ctl* ctl, int nf_in, float hscale, cudaStream_t st);
 // fused shift update (kernel (d)): V_{k+1} = W S; for active shifts
 // X_j += P_j Ut_j and P_j <- V_{k+1} - P_j LhT_j.  P and X hold s blocks of
 // m fields of ldw elements (field-major, like every other block).
@@ -82,15 +83,17 @@ void launch_shift_update(int prec, int wprec, void* Vnext, const void* W, const 
 // ---- small.cu ---------------------------------------------------------------
 struct SmallState;     // device m x m state (FP64 or double-float), defined in small.cu
 size_t small_state_bytes(int s);
+// sfp64: FP64 m x m scalar (else double-float); wprec: precision of the Gram
+// partials and coefficient copies (P64 for FP64 storage, else P32)
 void launch_small_init(SmallState* ss, Ctl* ctl, const double2* G0, const double* ref, int m, int s, double dtol,
-                       int wprec, cudaStream_t st);
+                       int sfp64, cudaStream_t st);
 // alpha_k from the Gram partials of V_k^H Y (+ coefficient tiles for the block update)
 void launch_small_alpha(SmallState* ss, const Ctl* ctl, const double* partials, int nblk, int nf_max,
-                        int wprec, void* coef_a, void* coef_bh, cudaStream_t st);
+                        int wprec, int sfp64, void* coef_a, void* coef_bh, cudaStream_t st);
 // W^H W from the Gram partials, pivoted QR with deflation, per-shift recurrences
 void launch_small_step(SmallState* ss, Ctl* ctl, const double* partials, int nblk, int s, int m,
                        double dtol, const double* sigma_dev, const double* target_dev, int freeze,
-                       int wprec, void* coefS_w, void* coefU_w, void* coefL_w, int* active,
+                       int wprec, int sfp64, void* coefS_w, void* coefU_w, void* coefL_w, int* active,
                        int* conv_step, double* res_out, cudaStream_t st);
 void launch_small_finish(SmallState* ss, Ctl* ctl, int s, int m, const int* active, cudaStream_t st);
 const double2* small_state_S(const SmallState* ss);

@@ -29,7 +29,8 @@
 //
 // Arithmetic.  With FP64 storage these kernels run in FP64.  With the
 // reduced storages they run in double-float (dd: pairs of FP32 words, 48-bit
-// significands): GB300 issues FP64 at 1/64 of its FP32 rate, so one FP64
+// significands) unless FP64 is requested: GB300 issues FP64 at 1/64 of its
+// FP32 rate, so one FP64
 // instruction occupies an SM sub-partition for about 64 cycles and these
 // latency-bound m x m kernels were dominated by it; the double-float forms
 // run on the FP32 pipes and keep far more accuracy than the FP32 Gram
@@ -380,9 +381,9 @@ __device__ __forceinline__ void reduce_store(T* G, int ld, typename Sc<T>::R* di
 
 // Sum the per-CTA Gram partials ([tile][blk][36], fixed order) into G (ld,
 // hermitian fill when herm) and the |y|^2 diagonal; all threads of the CTA.
-// FP64 state: FP64 partials summed in FP64.  Double-float state: FP32
-// partials (they carry FP32 accuracy) summed with compensated (Kahan) FP32
-// additions, the chains combined in double-float.  Consecutive threads take
+// FP64 partials (FP64 storage) are summed in FP64; FP32 partials (reduced
+// storage; they carry FP32 accuracy) with compensated (Kahan) FP32
+// additions, the chains combined in the state's scalar.  Consecutive threads take
 // consecutive slots (coalesced rows of 36); when the CTA has threads to spare,
 // ng groups split the CTAs' range and their sums are added in group order;
 // RC interleaved accumulators per thread keep several loads in flight (the
@@ -390,7 +391,7 @@ __device__ __forceinline__ void reduce_store(T* G, int ld, typename Sc<T>::R* di
 // Fixed order: bitwise reproducible.
 template <class T>
 __device__ void reduce_partials(const double* __restrict__ part, int nblk, int nf_max, int herm, T* G, int ld,
-                                typename Sc<T>::R* diag) {
+                                typename Sc<T>::R* diag, bool fp64_part) {
     using S = Sc<T>;
     using R = typename S::R;
     const int Tt = (nf_max + 3) / 4;
@@ -406,7 +407,7 @@ __device__ void reduce_partials(const double* __restrict__ part, int nblk, int n
         const size_t off = (size_t)tile * nblk * GSL + q;
         constexpr int RC = 8;
         R s;
-        if constexpr (is_fp64<T>()) {
+        if (fp64_part) {
             const double* p = part + off;
             double a[RC];
 #pragma unroll
@@ -419,7 +420,7 @@ __device__ void reduce_partials(const double* __restrict__ part, int nblk, int n
             double t = 0.0;
 #pragma unroll
             for (int r = 0; r < RC; ++r) t += a[r];
-            s = t;
+            s = S::r(t);
         } else {
             const float* p = reinterpret_cast<const float*>(part) + off;
             float sum[RC], comp[RC];
@@ -522,7 +523,7 @@ __global__ void small_alpha_kernel(SmallStateT<T>* ss, const Ctl* __restrict__ c
     if (ctl->done) return;
     __shared__ T A[M_MAX * M_MAX];
     __shared__ R yy[M_MAX];
-    reduce_partials<T>(part, nblk, nf_max, 0, A, M_MAX, yy);
+    reduce_partials<T>(part, nblk, nf_max, 0, A, M_MAX, yy, wprec == P64);
     __syncthreads();
     const int mk_ = ctl->mk, mp = ctl->k > 1 ? ctl->mprev : 0;
     const R half = S::r(0.5);
@@ -574,7 +575,7 @@ __global__ void small_step_kernel(SmallStateT<T>* ss, Ctl* ctl, const double* __
     int* perm = (int*)(rf + MM);
     const int j = blockIdx.x;
     const int k = ctl->k, mk_ = ctl->mk, mp = k > 1 ? ctl->mprev : 0;
-    reduce_partials<T>(part, nblk, m, 1, G, MM, nullptr);
+    reduce_partials<T>(part, nblk, m, 1, G, MM, nullptr, wprec == P64);
     const R* yys = reinterpret_cast<const R*>(ss->sh.yy);
     for (int i = threadIdx.x; i < mk_; i += blockDim.x) rf[i] = yys[i];
     for (int t = threadIdx.x; t < MM * MM; t += blockDim.x) Bn[t] = cz<T>();
@@ -719,29 +720,31 @@ SmallStateT<T>* as_state(SmallState* ss) { return reinterpret_cast<SmallStateT<T
 
 }  // namespace
 
-// the FP64 scalar for FP64 storage (wprec == P64), double-float otherwise
+// sfp64: FP64 m x m scalar (FP64 storage, or reduced storage on request),
+// otherwise double-float; wprec: precision of the Gram partials (FP64 for
+// FP64 storage, else FP32) and of the coefficient copies
 void launch_small_init(SmallState* ss, Ctl* ctl, const double2* G0, const double* ref, int m, int s, double dtol,
-                       int wprec, cudaStream_t st) {
+                       int sfp64, cudaStream_t st) {
     size_t sm = 4 * (size_t)m * m * sizeof(double2) + M_MAX * sizeof(int) + 2 * M_MAX * sizeof(double);
-    if (wprec == P64)
+    if (sfp64)
         small_init_kernel<double2><<<1, WS, sm, st>>>(as_state<double2>(ss), ctl, G0, ref, m, s, dtol);
     else
         small_init_kernel<ddc><<<1, WS, sm, st>>>(as_state<ddc>(ss), ctl, G0, ref, m, s, dtol);
 }
 
 void launch_small_alpha(SmallState* ss, const Ctl* ctl, const double* partials, int nblk, int nf_max, int wprec,
-                        void* coef_a, void* coef_bh, cudaStream_t st) {
-    if (wprec == P64)
+                        int sfp64, void* coef_a, void* coef_bh, cudaStream_t st) {
+    if (sfp64)
         small_alpha_kernel<double2><<<1, NT, 0, st>>>(as_state<double2>(ss), ctl, partials, nblk, nf_max, wprec,
-                                                       coef_a, coef_bh);
+                                                      coef_a, coef_bh);
     else
         small_alpha_kernel<ddc><<<1, NT, 0, st>>>(as_state<ddc>(ss), ctl, partials, nblk, nf_max, wprec, coef_a,
-                                                   coef_bh);
+                                                  coef_bh);
 }
 
 void launch_small_step(SmallState* ss, Ctl* ctl, const double* partials, int nblk, int s, int m, double dtol,
-                       const double* sigma_dev, const double* target_dev, int freeze, int wprec, void* coefS_w,
-                       void* coefU_w, void* coefL_w, int* active, int* conv_step, double* res_out,
+                       const double* sigma_dev, const double* target_dev, int freeze, int wprec, int sfp64,
+                       void* coefS_w, void* coefU_w, void* coefL_w, int* active, int* conv_step, double* res_out,
                        cudaStream_t st) {
     const int MM = m;                  // block widths never exceed the initial width m
     static bool attr_set = false;
@@ -752,7 +755,7 @@ void launch_small_step(SmallState* ss, Ctl* ctl, const double* partials, int nbl
                              (int)step_smem(M_MAX));
         attr_set = true;
     }
-    if (wprec == P64)
+    if (sfp64)
         small_step_kernel<double2><<<s, NT, step_smem(MM), st>>>(as_state<double2>(ss), ctl, partials, nblk, m, dtol,
                                                                  sigma_dev, target_dev, freeze, wprec, coefS_w,
                                                                  coefU_w, coefL_w, active, conv_step, res_out, MM);

@@ -74,6 +74,7 @@ struct Lane {
     int* h_conv = nullptr;                        // pinned
     // the inner solve in progress
     int m_in = 0, s_in = 0, prec = 0, step = 0, max_steps = 0, freeze = 0, poll_every = 1;
+    int sfp64 = 1;                                // m x m scalar: FP64 (1) or double-float (0)
     double dtol = 0;
     bool running = false;
 };
@@ -465,7 +466,7 @@ struct InnerResult {
 // result.  All work of a lane runs on its stream.
 dsbcg_status lane_start(dsbcg_ctx* c, Lane& L, const void* rhs, int rhs_prec, size_t rhs_ld, int m_in,
                         const double* sig, int s_in, const double* targets, int prec, double dtol, int max_steps,
-                        int freeze, int poll_every) {
+                        int freeze, int poll_every, int sfp64) {
     const int wp = work_prec(prec);
     const size_t ld = c->ld, n = c->n;
     const size_t fb = prec_elem_bytes(prec) * ld;
@@ -484,13 +485,13 @@ dsbcg_status lane_start(dsbcg_ctx* c, Lane& L, const void* rhs, int rhs_prec, si
     {
         Prof p(c, DSBCG_KCLASS_SMALL, 2, st);
         launch_gram_reduce(L.partials, L.nblk, m_in, 1, 1, L.G, L.diag, nullptr, m_in, rhs_prec != P64, st);
-        launch_small_init(L.ss, L.ctl, L.G, L.diag, m_in, s_in, dtol, wp, st);
+        launch_small_init(L.ss, L.ctl, L.G, L.diag, m_in, s_in, dtol, sfp64, st);
     }
     char* ring = (char*)L.vring;
     {
         Prof p(c, DSBCG_KCLASS_OTHER, 1, st);
         launch_init_basis(prec, ring + 1 * (size_t)m_in * fb, ld, rhs, rhs_prec, rhs_ld, n, small_state_S(L.ss),
-                          L.ctl, m_in, c->hscale, st);
+                          !sfp64, L.ctl, m_in, c->hscale, st);
     }
     c->kbytes[DSBCG_KCLASS_GRAM] += (double)m_in * n * prec_elem_bytes(rhs_prec);
     c->kbytes[DSBCG_KCLASS_OTHER] += (double)m_in * n * (prec_elem_bytes(rhs_prec) + prec_elem_bytes(prec));
@@ -502,6 +503,7 @@ dsbcg_status lane_start(dsbcg_ctx* c, Lane& L, const void* rhs, int rhs_prec, si
     L.max_steps = max_steps;
     L.freeze = freeze;
     L.poll_every = poll_every;
+    L.sfp64 = sfp64;
     L.dtol = dtol;
     L.running = true;
     return DSBCG_OK;
@@ -531,7 +533,7 @@ dsbcg_status lane_enqueue(dsbcg_ctx* c, Lane& L) {
         }
         {
             Prof p(c, DSBCG_KCLASS_SMALL, 1, st);
-            launch_small_alpha(L.ss, L.ctl, L.partials, L.nblk, m_in, wp, L.coef_a, L.coef_bh, st);
+            launch_small_alpha(L.ss, L.ctl, L.partials, L.nblk, m_in, wp, L.sfp64, L.coef_a, L.coef_bh, st);
         }
         {
             Prof p(c, DSBCG_KCLASS_UPDATE, 1, st);
@@ -544,7 +546,7 @@ dsbcg_status lane_enqueue(dsbcg_ctx* c, Lane& L) {
         {
             Prof p(c, DSBCG_KCLASS_SMALL, 1, st);
             launch_small_step(L.ss, L.ctl, L.partials, L.nblk, s_in, m_in, L.dtol, L.sigma, L.target, L.freeze, wp,
-                              L.coefS, L.coefU, L.coefL, L.active, L.conv_step, L.res, st);
+                              L.sfp64, L.coefS, L.coefU, L.coefL, L.active, L.conv_step, L.res, st);
         }
         {
             Prof p(c, DSBCG_KCLASS_SHIFT, 1, st);
@@ -637,6 +639,7 @@ void dsbcg_params_default(dsbcg_params* p) {
     p->poll_every = 16;
     p->freeze_converged = 1;
     p->refine = 1;
+    p->fp64_residuals = 0;
 }
 
 const char* dsbcg_error_string(dsbcg_status s) {
@@ -800,9 +803,10 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
     const double dtol = prm.dtol > 0 ? prm.dtol : default_dtol(prec);
     const bool mixed = prec != P64;
     // true residuals, B and the accumulated solutions: FP64 fields for FP64
-    // storage, double-float fields (FP32 arithmetic, 48-bit significands)
-    // for the reduced storages
-    const int hp = mixed ? PDD : P64;
+    // storage (or on request), double-float fields (FP32 arithmetic, 48-bit
+    // significands) for the reduced storages; the m x m work likewise
+    const int sfp64 = (!mixed || prm.fp64_residuals) ? 1 : 0;
+    const int hp = sfp64 ? P64 : PDD;
     CKS(ensure_links(c, prec));
     CKS(ensure_links(c, hp));
     CKS(ensure_ws(c, m, s, prec));
@@ -883,7 +887,7 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
         InnerResult ir;
         Lane* L0 = &w.lanes[0];
         CKS(lane_start(c, *L0, w.B64, rprec, rld, m, sigma, s, tg.data(), prec, dtol, prm.max_block_steps,
-                       prm.freeze_converged, prm.poll_every));
+                       prm.freeze_converged, prm.poll_every, sfp64));
         CKS(run_lanes(c, &L0, 1));
         CKS(lane_finish(c, *L0, &ir, 0, conv.data()));
         total_steps += ir.steps;
@@ -987,7 +991,7 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
                 CK(cudaStreamWaitEvent(L.st, L.ready, 0));
             }
             CKS(lane_start(c, L, L.rhs, rprec, rld, mu, &sigma[j], 1, tg.data(), prec, dtol,
-                           std::max(1, prm.max_block_steps - total_steps), prm.freeze_converged, prm.poll_every));
+                           std::max(1, prm.max_block_steps - total_steps), prm.freeze_converged, prm.poll_every, sfp64));
             CKS(lane_enqueue(c, L));
             restarts += 1;
             lane_j[li] = j;

@@ -41,7 +41,8 @@ class Params(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("dtol", ctypes.c_double),
                 ("max_block_steps", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("restart_drop", ctypes.c_double), ("poll_every", ctypes.c_int),
-                ("freeze_converged", ctypes.c_int), ("refine", ctypes.c_int)]
+                ("freeze_converged", ctypes.c_int), ("refine", ctypes.c_int),
+                ("fp64_residuals", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -158,7 +159,7 @@ class Context:
 
     def solve(self, B, sigma, tol, storage="fp32", out=None, dtol=0.0, max_block_steps=None,
               max_restarts=None, restart_drop=None, poll_every=None, freeze=True, refine=True,
-              raise_on_error=True):
+              fp64_residuals=False, raise_on_error=True):
         """X (s, m, n) complex128 for (sigma_j + A) X_j = B; B (m, n) complex128.
 
         B and out may live on the GPU or on the host; the result has B's device.
@@ -186,6 +187,7 @@ class Context:
             p.poll_every = int(poll_every)
         p.freeze_converged = int(bool(freeze))
         p.refine = int(bool(refine))
+        p.fp64_residuals = int(bool(fp64_residuals))
         rel = np.zeros((s, m), dtype=np.float64)
         conv = np.zeros((s, m), dtype=np.int32)
         st = Stats()

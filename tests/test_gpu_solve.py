@@ -1,7 +1,8 @@
 """GPU DSBlockCG parity against the FP64 oracle, through the C ABI.
 
-* 4^4 workload (b_4 = b_1 + b_2): FP64 and mixed precisions against dense LU
-  (relative error <= 1e-7 per (rhs, shift)), exact deflation, x_4 = x_1 + x_2;
+* 4^4 workload (b_4 = b_1 + b_2): FP64 and mixed precisions (double-float
+  or FP64 reliable updates) against dense LU (relative error <= 1e-7 per
+  (rhs, shift)), exact deflation, x_4 = x_1 + x_2;
 * fixed number of block steps: the GPU iterate equals the block Galerkin
   iterate of Eq. 3.2 computed by the oracle's definition;
 * special cases m = s = 1 (CG), sigma = 0, a ragged lattice whose volume is
@@ -39,12 +40,13 @@ def _relerr(X, Xd):
     return np.linalg.norm(X - Xd, axis=-1) / np.linalg.norm(Xd, axis=-1)
 
 
-@pytest.mark.parametrize("storage,tol,bound", [("fp64", 1e-10, 1e-7), ("fp32", 1e-10, 1e-7),
-                                               ("fp16", 1e-10, 1e-7), ("bf16", 1e-8, 1e-5)])
-def test_w1_against_dense_lu(w1, storage, tol, bound):
+@pytest.mark.parametrize("storage,tol,bound,fp64res", [("fp64", 1e-10, 1e-7, False), ("fp32", 1e-10, 1e-7, False),
+                                                       ("fp32", 1e-10, 1e-7, True), ("fp16", 1e-10, 1e-7, False),
+                                                       ("bf16", 1e-8, 1e-5, False)])
+def test_w1_against_dense_lu(w1, storage, tol, bound, fp64res):
     wl, Ad, Xd, ctx = w1
     B = torch.from_numpy(wl["B"]).to(DEV)
-    X, st = ctx.solve(B, wl["sigma"], tol, storage=storage)
+    X, st = ctx.solve(B, wl["sigma"], tol, storage=storage, fp64_residuals=fp64res)
     Xg = X.cpu().numpy()
     assert st["code"] == 0, st
     assert st["true_relres"].max() <= tol
@@ -145,10 +147,11 @@ def w2():
     ctx.close()
 
 
-def test_w2_full_size_mixed(w2):
+@pytest.mark.parametrize("fp64res", [False, True])
+def test_w2_full_size_mixed(w2, fp64res):
     wl, ctx = w2
     B = torch.from_numpy(wl["B"]).to(DEV)
-    X, st = ctx.solve(B, wl["sigma"], wl["tol"], storage="fp32")
+    X, st = ctx.solve(B, wl["sigma"], wl["tol"], storage="fp32", fp64_residuals=fp64res)
     assert st["code"] == 0, st
     assert st["true_relres"].max() <= wl["tol"]
     # independent check with the oracle's operator on sampled systems
@@ -157,8 +160,8 @@ def test_w2_full_size_mixed(w2):
         r = wl["B"][i] - wl["sigma"][j] * x - W.A_vec(wl["U"], wl["kappa"], wl["dims"], x)
         rel = np.linalg.norm(r) / np.linalg.norm(wl["B"][i])
         assert rel <= 10 * wl["tol"], (j, i, rel)
-        # the library's double-float true residual agrees with the oracle's
-        # FP64 recomputation far below tol
+        # the library's true residual (double-float, or FP64 on request)
+        # agrees with the oracle's FP64 recomputation far below tol
         assert abs(rel - st["true_relres"][j, i]) <= 1e-2 * wl["tol"], (j, i, rel, st["true_relres"][j, i])
 
 
