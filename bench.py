@@ -375,7 +375,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--cpu-vectors", type=int, default=2)
     ap.add_argument("--ref-vectors", type=int, default=1)
-    ap.add_argument("--ref-total-vectors", type=int, default=4200)
+    # single-vector A applications of a whole FP64 solve of the workload (the
+    # plain FP64 GPU form measured 1488 on 16^3 x 32, m = s = 12); the main
+    # line's cpu_baseline scales its sample by the same count
+    ap.add_argument("--ref-total-vectors", type=int, default=1488)
     ap.add_argument("--lattice", type=lambda t: tuple(int(x) for x in t.split(",")), default=None,
                     help="Lx,Ly,Lz,Lt to resize the workload (profiling of smaller cases)")
     args = ap.parse_args()
