@@ -291,7 +291,19 @@ int ensure_refine_lanes(dsbcg_ctx* c, int want) {
     const int m = w.m, prec = w.prec;
     const size_t fb = prec_elem_bytes(prec) * c->ld, wb = prec_elem_bytes(work_prec(prec)) * c->ld;
     const size_t db = sizeof(double2) * c->ld, tb = M_MAX * M_MAX * sizeof(double2);
+    // a lane's buffers; lanes stop while a tenth of the device (at least
+    // 4 GiB) would still be free, so that large lattices keep memory for the
+    // caller
+    const size_t lane_bytes = 4 * m * fb + 2 * m * wb + m * db + gram_partial_doubles(M_MAX) * sizeof(double) +
+                              small_state_bytes(1) + 6 * tb;
     while ((int)w.lanes.size() < want) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            cudaGetLastError();
+            break;
+        }
+        const size_t reserve = std::max(tot / 10, (size_t)4 << 30);
+        if (fr < lane_bytes + reserve) break;
         Lane L;
         bool ok = dmalloc(c, &L.vring, 2 * m * fb) == DSBCG_OK && dmalloc(c, &L.zw, m * fb) == DSBCG_OK &&
                   dmalloc(c, &L.y, m * fb) == DSBCG_OK && dmalloc(c, &L.P, m * wb) == DSBCG_OK &&
