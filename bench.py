@@ -303,6 +303,45 @@ def run_ours(args):
             "max_true_relres": float(max(st["true_relres"].max() for st in stf)),
             "note": "FP32 storage; true residuals, solution accumulation and m x m work in IEEE FP64"}
 
+    # gauge-link force of the gradient workload (16^3 x 32, m = s = 8, FP32):
+    # dsbcg_force on device X and adjoint Lambda, whole call and force kernel
+    if rank == 0 and not args.no_force:
+        wf = synth.make_workload("w4_force_16x16x16x32")
+        fctx = dsbcg.Context(wf["dims"], torch.from_numpy(wf["U"]).to(dev), wf["kappa"], stream=stream)
+        fm, fs = wf["B"].shape[0], len(wf["sigma"])
+        fn = wf["B"].shape[1]
+        g = torch.Generator(device=dev).manual_seed(44)
+        Xf = torch.randn((fs, fm, fn), dtype=torch.complex128, device=dev, generator=g)
+        Lf = torch.randn((fs, fm, fn), dtype=torch.complex128, device=dev, generator=g)
+        dU = fctx.force(Xf, Lf, wf["weights"], storage="fp32")
+        torch.cuda.synchronize(dev)
+        nfr = 3
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(nfr):
+            fctx.force(Xf, Lf, wf["weights"], storage="fp32", out=dU)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        call_ms = e0.elapsed_time(e1) / nfr
+        fctx.set_profiling(True)
+        fctx.read_profile()
+        fctx.force(Xf, Lf, wf["weights"], storage="fp32", out=dU)
+        kst, _ = fctx.read_profile()
+        fctx.set_profiling(False)
+        nf = fs * fm
+        V = fn // 12
+        # force kernel: four FP32 fields of nf spinors in, 36 FP64 link entries per site out
+        fbytes = 4.0 * nf * fn * 8 + V * 36 * 16
+        kms = kst.get("other", 0.0)
+        line["force"] = {
+            "workload": "w4_force 16x16x16x32, m=8, s=8, FP32 storage",
+            "ms_per_call": round(call_ms, 3), "kernel_ms": round(kms, 3),
+            "kernel_GBps": round(fbytes / (kms / 1e3) / 1e9, 1) if kms > 0 else None,
+            "kernel_frac_of_hbm": round(fbytes / (kms / 1e3) / 1e9 / peak, 4) if kms > 0 else None,
+            "note": "call = pack X and Lambda to FP32, D on both, force kernel, dU out (device buffers)"}
+        fctx.close()
+        del Xf, Lf, dU
+
     fp64_mvms = None
     if rank == 0 and not args.no_fp64:
         torch.cuda.synchronize(dev)
@@ -375,6 +414,7 @@ def main():
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16", "fp64"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--no-force", action="store_true", help="skip the gauge-force timing")
     ap.add_argument("--cpu-vectors", type=int, default=2)
     ap.add_argument("--ref-vectors", type=int, default=1)
     # single-vector A applications of a whole FP64 solve of the workload (the

@@ -218,6 +218,12 @@ dsbcg_status dsbcg_force(dsbcg_ctx* ctx, int m, int s, const void* X, const void
 /* Per-kernel CUDA-event timing inside dsbcg_solve (off by default). */
 dsbcg_status dsbcg_set_profiling(dsbcg_ctx* ctx, int on);
 
+/* Per-class CUDA-event time (ms, classes as in dsbcg_stats.kernel_ms) and
+ * launch counts accumulated while profiling was on, since the last read or
+ * the start of the last dsbcg_solve; resets them.  Either pointer may be
+ * NULL.  Serves calls without a stats argument (dsbcg_force, dsbcg_apply). */
+dsbcg_status dsbcg_read_profile(dsbcg_ctx* ctx, double kernel_ms[8], long long kernel_launches[8]);
+
 void dsbcg_destroy(dsbcg_ctx* ctx);
 const char* dsbcg_error_string(dsbcg_status status);
 

@@ -744,6 +744,20 @@ dsbcg_status dsbcg_set_profiling(dsbcg_ctx* c, int on) {
     return DSBCG_OK;
 }
 
+dsbcg_status dsbcg_read_profile(dsbcg_ctx* c, double kernel_ms[8], long long kernel_launches[8]) {
+    if (!c) return DSBCG_ERR_ARG;
+    CK(cudaStreamSynchronize(c->st));
+    prof_collect(c);
+    for (int q = 0; q < 8; ++q) {
+        if (kernel_ms) kernel_ms[q] = c->kms[q];
+        if (kernel_launches) kernel_launches[q] = c->klaunch[q];
+        c->kms[q] = 0;
+        c->klaunch[q] = 0;
+        c->kbytes[q] = 0;
+    }
+    return DSBCG_OK;
+}
+
 dsbcg_status dsbcg_apply(dsbcg_ctx* c, int op, int storage, int m, const void* in, void* out) {
     if (!c || !in || !out || m < 1 || m > 4096 || op < 0 || op > 2 || storage < 0 || storage > PDD)
         return DSBCG_ERR_ARG;

@@ -157,6 +157,14 @@ class Context:
     def set_profiling(self, on=True):
         _check(lib().dsbcg_set_profiling(self._ctx, int(bool(on))), "dsbcg_set_profiling")
 
+    def read_profile(self):
+        """dsbcg_read_profile: {class: ms} and {class: launches} since the
+        last read (or solve); resets them."""
+        ms = (ctypes.c_double * 8)()
+        nl = (ctypes.c_longlong * 8)()
+        _check(lib().dsbcg_read_profile(self._ctx, ms, nl), "dsbcg_read_profile")
+        return ({KCLASS[q]: ms[q] for q in range(7)}, {KCLASS[q]: nl[q] for q in range(7)})
+
     def solve(self, B, sigma, tol, storage="fp32", out=None, dtol=0.0, max_block_steps=None,
               max_restarts=None, restart_drop=None, poll_every=None, freeze=True, refine=True,
               fp64_residuals=False, raise_on_error=True):
