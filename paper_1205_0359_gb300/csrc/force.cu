@@ -16,10 +16,21 @@ namespace dsbcg {
 
 namespace {
 
+// the 12 components of site x: six 16-byte pair chunks for FP32 fields
 template <int P>
 __device__ __forceinline__ void load_sp(const typename Tr<P>::S2* f, size_t V, size_t x, typename Tr<P>::C p[12]) {
+    if constexpr (P == P32) {
+        const float4* q = reinterpret_cast<const float4*>(f);
 #pragma unroll
-    for (int c = 0; c < 12; ++c) p[c] = Elem<P>::ld(f, fidx<P>(V, x, c), 1);
+        for (int c = 0; c < 6; ++c) {
+            const float4 v = __ldg(q + (size_t)c * V + x);
+            p[2 * c] = make_float2(v.x, v.y);
+            p[2 * c + 1] = make_float2(v.z, v.w);
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 12; ++c) p[c] = Elem<P>::ld(f, fidx<P>(V, x, c), 1);
+    }
 }
 
 // q = (1 - gamma_mu) p (fwd) or (1 + gamma_mu) p, full 4-spinor, chiral basis
@@ -47,8 +58,8 @@ __device__ __forceinline__ void project(int mu, bool minus, const C p[12], C q[1
     }
 }
 
-template <class C>
-__device__ __forceinline__ void outer_acc(C acc[9], const C pa[12], const C qb[12], double w) {
+template <class C, class R>
+__device__ __forceinline__ void outer_acc(C acc[9], const C pa[12], const C qb[12], R w) {
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -56,8 +67,8 @@ __device__ __forceinline__ void outer_acc(C acc[9], const C pa[12], const C qb[1
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
                 C t = cmulc(qb[s * 3 + b], pa[s * 3 + a]);      // conj(q_b) p_a
-                acc[a * 3 + b].x = fma((decltype(t.x))w, t.x, acc[a * 3 + b].x);
-                acc[a * 3 + b].y = fma((decltype(t.x))w, t.y, acc[a * 3 + b].y);
+                acc[a * 3 + b].x = fma(w, t.x, acc[a * 3 + b].x);
+                acc[a * 3 + b].y = fma(w, t.y, acc[a * 3 + b].y);
             }
 }
 
@@ -89,7 +100,7 @@ __global__ void __launch_bounds__(256) force_kernel(double2* __restrict__ dU, co
 #pragma unroll
     for (int q = 0; q < 9; ++q) acc[q] = mk(R(0), R(0));
     for (int k = 0; k < nf; ++k) {
-        const double w = wf[k];
+        const R w = (R)wf[k];            // one conversion per field (FP64 -> FP32 is slow on GB300)
         const size_t off = (size_t)k * ld;
         for (int pair = 0; pair < 2; ++pair) {
             const typename Tr<P>::S2* fa = (pair == 0 ? A : Cf) + off;
