@@ -555,18 +555,17 @@ __global__ void __launch_bounds__(256) v_update_kernel(typename Tr<P>::S2* __res
 
 // Per-shift update of one row tile: X_j += P_j Ut_j, P_j <- V_{k+1} - P_j Lh_j.
 // One CTA per (row tile, shift), shift index fastest so that the CTAs that
-// read the same V_{k+1} tile run together and share it through L2.  The
-// tiles of V_{k+1}, P_j and X_j (one contiguous run of ROWS elements per
-// field) arrive in shared memory by bulk asynchronous copies completing on
-// one mbarrier; many small independent CTAs per SM overlap their copies and
-// their arithmetic.  Results are stored directly (coalesced).  The mbarrier
-// wait is bounded: on timeout the CTA records an error in the control block
-// and returns after draining its copies.  At k == 1 the search block is
-// P_j = V_1 (the current block, storage precision).
+// read the same V_{k+1} tile run together and share it through L2.  The P_j
+// and X_j tiles (one contiguous run of ROWS elements per field) arrive in
+// shared memory by bulk asynchronous copies completing on one mbarrier;
+// V_{k+1} rows are read straight from L2, which keeps the shared memory per
+// CTA small and the resident CTAs per SM many.  Results are stored directly
+// (coalesced).  The mbarrier wait is bounded: on timeout the CTA records an
+// error in the control block and returns after draining its copies.  At
+// k == 1 the search block is P_j = V_1 (the current block, storage precision).
 template <int NF, int PW, int PS>
 __host__ __device__ constexpr size_t su_smem_bytes(int rows) {
-    return (size_t)rows * NF * (sizeof(typename Tr<PS>::S2) + 2 * sizeof(typename Tr<PW>::S2))
-           + 2 * (size_t)NF * NF * sizeof(typename Tr<PW>::C) + 16;
+    return (size_t)rows * NF * 2 * sizeof(typename Tr<PW>::S2) + 2 * (size_t)NF * NF * sizeof(typename Tr<PW>::C) + 16;
 }
 
 // rows per thread of shift_tile_kernel: one (two rows per thread halve the
@@ -589,8 +588,7 @@ __global__ void __launch_bounds__(ROWS / su_rpt(NF, PW)) shift_tile_kernel(
     if (!active[j]) return;
     const int mk_ = ctl->mk, mn = ctl->mnext, k = ctl->k;
     extern __shared__ __align__(128) unsigned char su_smem[];
-    SE* sV = reinterpret_cast<SE*>(su_smem);                        // [NF][ROWS] V_{k+1} (or V_1 at k == 1)
-    E* sP = reinterpret_cast<E*>(su_smem + (size_t)NF * ROWS * sizeof(SE));
+    E* sP = reinterpret_cast<E*>(su_smem);                          // [NF][ROWS] P_j (or V_1 at k == 1)
     E* sX = sP + NF * ROWS;
     C* sU = reinterpret_cast<C*>(sX + NF * ROWS);
     C* sL = sU + NF * NF;
@@ -608,11 +606,10 @@ __global__ void __launch_bounds__(ROWS / su_rpt(NF, PW)) shift_tile_kernel(
     }
     __syncthreads();
     if (tid == 0) {
-        // k == 1: the search block is V_1 itself (loaded into sP's place via sV below)
-        const uint32_t nv = (uint32_t)mn + (k == 1 ? (uint32_t)mk_ : 0u);
+        // k == 1: the search block is V_1 itself (loaded into sP's place)
+        const uint32_t nv = k == 1 ? (uint32_t)mk_ : 0u;
         const uint32_t np = k > 1 ? (uint32_t)mk_ : 0u;
         mbar_expect_tx(bar, nv * tbs + (np + (uint32_t)m) * tb);
-        for (int c = 0; c < mn; ++c) bulk_g2s(sV + c * ROWS, Vn + (size_t)c * ld + e0, tbs, bar);
         if (k == 1) {
             // V_1 (storage precision) into the P tile's space, which is at least as large
             for (int a = 0; a < mk_; ++a) bulk_g2s(reinterpret_cast<SE*>(sP) + a * ROWS, Vk + (size_t)a * ld + e0, tbs, bar);
@@ -692,7 +689,14 @@ __global__ void __launch_bounds__(ROWS / su_rpt(NF, PW)) shift_tile_kernel(
 #pragma unroll
     for (int q = 0; q < RPT; ++q)
 #pragma unroll
-        for (int c = 0; c < NF; ++c) pn[q][c] = c < mn ? ldv(sV, c, ok_[q] ? rr_[q] : 0) : mk(R(0), R(0));
+        for (int c = 0; c < NF; ++c) {
+            if (c < mn) {
+                const auto v = Elem<P>::ld(Vn + (size_t)c * ld, e0 + (ok_[q] ? rr_[q] : 0), inv);
+                pn[q][c] = mk(R(v.x), R(v.y));
+            } else {
+                pn[q][c] = mk(R(0), R(0));
+            }
+        }
 #pragma unroll
     for (int a = 0; a < NF; ++a) {
 #pragma unroll
