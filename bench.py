@@ -53,7 +53,7 @@ def workload_config(wl, storage):
         "workload": (f"{WORKLOAD}: Wilson D^H D on {'x'.join(map(str, wl['dims']))}, kappa {wl['kappa']}, "
                      f"m={wl['B'].shape[0]} Z2 RHS, s={len(wl['sigma'])} shifts "
                      f"{wl['sigma'][0]:.0e}..{wl['sigma'][-1]:.0e}, true residual <= {wl['tol']:.0e}, "
-                     f"{storage} storage + FP64 restarts"),
+                     f"{storage} storage + {'FP64' if storage == 'fp64' else 'double-float'} reliable updates"),
         "lattice": list(wl["dims"]), "m": int(wl["B"].shape[0]), "s": int(len(wl["sigma"])),
         "tol": wl["tol"], "storage": storage,
         "l2": "no flush: one block step streams ~9 GB, far above the 129 MB L2",

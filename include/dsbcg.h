@@ -81,7 +81,7 @@ typedef struct {
     double dtol;            /* deflation threshold relative to a direction's norm when
                                created; <= 0 selects the default for the precision */
     int max_block_steps;    /* cap on block Lanczos steps over the whole solve */
-    int max_restarts;       /* cap on FP64 true-residual restarts */
+    int max_restarts;       /* cap on true-residual restarts */
     double restart_drop;    /* an inner solve stops once every estimated residual has
                                dropped by this factor (mixed precision only) */
     int poll_every;         /* block steps between host reads of the convergence flags */
@@ -98,10 +98,10 @@ typedef struct {
     int block_steps;        /* block Lanczos steps, all inner solves */
     long long mvms;         /* A applications to single vectors (one D plus one D^H each) */
     int deflations;         /* directions dropped by deflation */
-    int restarts;           /* FP64 true-residual restarts */
+    int restarts;           /* true-residual restarts */
     int final_rank;         /* block width m_k at the end of the last inner solve */
     double seconds;         /* wall time of the call */
-    double* true_relres;    /* caller-provided [s][m] or NULL: final FP64 true
+    double* true_relres;    /* caller-provided [s][m] or NULL: final true
                                residual ||b_i - (sigma_j + A) x_ij|| / ||b_i|| */
     int* conv_step;         /* caller-provided [s][m] or NULL: block step at which
                                (i, j) met its inner target (-1: never) */
@@ -119,7 +119,7 @@ typedef struct {
 #define DSBCG_KCLASS_UPDATE 2       /* block update W = Y - V a - V' b^H (+ Gram) */
 #define DSBCG_KCLASS_SHIFT 3        /* fused shift update (V, P_j, X_j) */
 #define DSBCG_KCLASS_SMALL 4        /* FP64 m x m kernels */
-#define DSBCG_KCLASS_RESIDUAL 5     /* FP64 true residual */
+#define DSBCG_KCLASS_RESIDUAL 5     /* true residuals (FP64 or double-float) */
 #define DSBCG_KCLASS_OTHER 6
 
 /* Fill *p with the defaults (FP32 storage, automatic dtol, freezing on). */

@@ -72,9 +72,10 @@ void launch_block_update(int prec, void* W, const void* Y, const void* Vk, const
 // or double-float when s_dd)
 void launch_init_basis(int prec, void* V1, size_t ldv, const void* B, int bprec, size_t ldb, size_t n,
                        const double2* S, int s_dd, const Ctl* ctl, int nf_in, float hscale, cudaStream_t st);
-// fused shift update (kernel (d)): V_{k+1} = W S; for active shifts
-// X_j += P_j Ut_j and P_j <- V_{k+1} - P_j LhT_j.  P and X hold s blocks of
-// m fields of ldw elements (field-major, like every other block).
+// shift update (the per-shift short recurrences, Sec. 3): V_{k+1} = W S;
+// for active shifts X_j += P_j Ut_j and P_j <- V_{k+1} - P_j LhT_j.  P and X
+// hold s blocks of m fields of ldw elements (field-major, like every other
+// block).
 void launch_shift_update(int prec, int wprec, void* Vnext, const void* W, const void* Vk,
                          size_t ld, void* P, void* X, size_t ldw, size_t n, int s, int m,
                          Ctl* ctl, int nf_max, const void* coefS, const void* coefU,
