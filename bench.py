@@ -342,6 +342,9 @@ def run_ours(args):
         fctx.close()
         del Xf, Lf, dU
 
+    if rank == 0 and not args.no_compare:
+        line["comparison"] = run_comparison(dev, stream)
+
     fp64_mvms = None
     if rank == 0 and not args.no_fp64:
         torch.cuda.synchronize(dev)
@@ -372,6 +375,54 @@ def run_ours(args):
 
 
 # ------------------------------------------------------- reference arm --
+def run_comparison(dev, stream, name="cmp_16x16x16x16", storage="fp64", dims=None, m=None, s=None):
+    """The paper's algorithm comparison (Sec. 4, Table 1) on the same kernels:
+    CG = one solve per (rhs, shift), block CG = one solve per shift with all
+    right-hand sides, shifted CG = one solve per right-hand side with all
+    shifts, DSBlockCG = one joint solve.  Returns mvms, block steps and GPU
+    time per algorithm, and their ratios to DSBlockCG."""
+    import torch
+    from paper_1205_0359_gb300 import dsbcg, synth
+    wl = synth.make_workload(name, dims=dims, m=m, s=s)
+    ctx = dsbcg.Context(wl["dims"], torch.from_numpy(wl["U"]).to(dev), wl["kappa"], stream=stream)
+    B = torch.from_numpy(wl["B"]).to(dev)
+    sig = np.asarray(wl["sigma"])
+    m, s = B.shape[0], sig.size
+    plans = {
+        "CG": [(slice(i, i + 1), [j]) for i in range(m) for j in range(s)],
+        "BlockCG": [(slice(0, m), [j]) for j in range(s)],
+        "shiftedCG": [(slice(i, i + 1), list(range(s))) for i in range(m)],
+        "DSBlockCG": [(slice(0, m), list(range(s)))],
+    }
+    out = {}
+    for alg, runs in plans.items():
+        rows, shifts = runs[0]                                # warm-up (workspace of this shape)
+        ctx.solve(B[rows].contiguous(), sig[shifts], wl["tol"], storage=storage)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mv = steps = 0
+        worst = 0.0
+        for rows, shifts in runs:
+            _, st = ctx.solve(B[rows].contiguous(), sig[shifts], wl["tol"], storage=storage)
+            mv += st["mvms"]
+            steps += st["block_steps"]
+            worst = max(worst, float(st["true_relres"].max()))
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        out[alg] = {"mvms": int(mv), "block_steps": int(steps), "ms": round(e0.elapsed_time(e1), 2),
+                    "solves": len(runs), "max_true_relres": worst}
+    ref = out["DSBlockCG"]
+    for alg in out:
+        out[alg]["mvms_ratio"] = round(out[alg]["mvms"] / ref["mvms"], 3)
+        out[alg]["time_ratio"] = round(out[alg]["ms"] / ref["ms"], 3)
+    ctx.close()
+    return {"workload": f"{name}: Wilson D^H D on {'x'.join(map(str, wl['dims']))}, kappa {wl['kappa']}, "
+                        f"m={m} Gaussian RHS, "
+                        f"s={s} shifts {sig[0]:.0e}..{sig[-1]:.0e}, tol {wl['tol']:.0e}, {storage} storage",
+            "algorithms": out}
+
+
 def run_reference(args):
     """The FP64 CPU oracle on the host cores, as the reference implementation."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -415,6 +466,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-force", action="store_true", help="skip the gauge-force timing")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the paper's algorithm comparison (CG, block CG, shifted CG, DSBlockCG)")
     ap.add_argument("--cpu-vectors", type=int, default=2)
     ap.add_argument("--ref-vectors", type=int, default=1)
     # single-vector A applications of a whole FP64 solve of the workload (the

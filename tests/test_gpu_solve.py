@@ -180,3 +180,17 @@ def test_concurrent_restarts_match_serial(w1):
     assert stc["block_steps"] == sts["block_steps"]
     assert torch.equal(Xc, Xs)
     assert np.array_equal(stc["true_relres"], sts["true_relres"])
+
+
+def test_paper_comparison_special_cases():
+    """The paper's comparison (Sec. 4, Table 1) as special cases of the same
+    solver, on a small lattice: every system of every algorithm meets tol,
+    DSBlockCG needs the fewest A applications and plain CG the most."""
+    import bench
+    res = bench.run_comparison(DEV, torch.cuda.current_stream(), name="cmp_16x16x16x16", dims=(8, 8, 8, 8),
+                               m=3, s=4)["algorithms"]
+    for alg, r in res.items():
+        assert r["max_true_relres"] <= 1e-8, (alg, r)
+    mv = {alg: r["mvms"] for alg, r in res.items()}
+    assert mv["DSBlockCG"] == min(mv.values()), mv
+    assert mv["CG"] == max(mv.values()), mv
