@@ -163,6 +163,25 @@ def oracle_sample(wl, vectors, total_vectors):
     return systems / (per_vec * total_vectors), max(1, round(cpu / wall)), wall, per_vec
 
 
+# ------------------------------------------------------- replica timing --
+def max_over_ranks(x, world, device):
+    """The largest of a per-rank float over the process group (the job is as
+    slow as its slowest replica); x itself at world size 1."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world, m, s, solves, seconds):
+    """Whole-job (rhs x shift) systems/s of `world` independent replicas that
+    each ran `solves` solves of m x s systems in `seconds` (the slowest's)."""
+    return world * m * s * solves / seconds
+
+
 # ------------------------------------------------------------- our arm --
 def run_ours(args):
     import torch
@@ -204,13 +223,9 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    ms_total = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     ms_step = ms_total / args.steps
-    value = world * m * s * args.steps / (ms_total / 1e3)
+    value = replica_value(world, m, s, args.steps, ms_total / 1e3)
     maxrel = max(float(st["true_relres"].max()) for st in stats)
     ok = all(st["code"] == 0 for st in stats) and maxrel <= wl["tol"]
 
@@ -277,12 +292,8 @@ def run_ours(args):
     for _ in range(args.steps):
         solve(Bx=Bh, Xx=Xh)
     torch.cuda.synchronize(dev)
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    line["e2e"] = {"value": round(world * m * s / e2e_s, 3), "unit": UNIT,
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world, dev)
+    line["e2e"] = {"value": round(replica_value(world, m, s, 1, e2e_s), 3), "unit": UNIT,
                    "h2d_bytes_per_step": int(Bh.numel() * 16), "d2h_bytes_per_step": int(Xh.numel() * 16)}
 
     # the same mixed solve with IEEE FP64 reliable updates and m x m work
