@@ -194,3 +194,26 @@ def test_paper_comparison_special_cases():
     mv = {alg: r["mvms"] for alg, r in res.items()}
     assert mv["DSBlockCG"] == min(mv.values()), mv
     assert mv["CG"] == max(mv.values()), mv
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_wide_block_against_dense_lu(storage):
+    """m = 20 right-hand sides: block widths above 16 take the untiled Gram
+    kernel; solutions against dense LU on 4^4."""
+    dims = (4, 4, 4, 4)
+    rng = np.random.Generator(np.random.PCG64(77))
+    U = synth.su3_links(dims, 0.3, rng)
+    kappa = 0.12
+    n = 12 * synth.volume(dims)
+    B = synth.gaussian_rhs(n, 20, rng)
+    sigma = np.array([1e-2, 1.0])
+    Ad = W.dense_A(U, kappa, dims)
+    Xd = dense_solve(Ad, B, sigma)
+    ctx = dsbcg.Context(dims, torch.from_numpy(U).to(DEV), kappa)
+    try:
+        X, st = ctx.solve(torch.from_numpy(B).to(DEV), sigma, 1e-10, storage=storage)
+        assert st["code"] == 0, st["status"]
+        assert st["true_relres"].max() <= 1e-10
+        assert _relerr(X.cpu().numpy(), Xd).max() <= 1e-7
+    finally:
+        ctx.close()
