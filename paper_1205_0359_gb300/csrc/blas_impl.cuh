@@ -503,12 +503,8 @@ void launch_gram_tile_t(const void* X, const void* Y, size_t ld, size_t n, Ctl* 
     const int npb = ntiles_of(nf_max, herm);
     const int nbuf_fields = (X == Y) ? nf_max : 2 * nf_max;
     const size_t smem = GNST * (size_t)nbuf_fields * GR * sizeof(SE) + 2 * GNST * sizeof(uint64_t);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(gram_tile_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(GNST * 2 * 16 * GR * sizeof(SE) + 2 * GNST * sizeof(uint64_t)));
-        attr = true;
-    }
+    static std::atomic<unsigned long long> devs{0};
+    max_dyn_smem_once(gram_tile_kernel<P>, (int)(GNST * 2 * 16 * GR * sizeof(SE) + 2 * GNST * sizeof(uint64_t)), devs);
     gram_tile_kernel<P><<<nblk, (npb + 1) * 32, smem, st>>>((const SE*)X, (const SE*)Y, ld, n, ctl, nf_static, nf_max, herm,
                                                       diag_yy, partials, hscale);
 }
@@ -787,12 +783,8 @@ void launch_su_t(void* Vnext, const void* W, const void* Vk, size_t ld, void* Pp
         v_update_kernel<P, NF><<<(unsigned)((n + 255) / 256), 256, 0, st>>>((S2*)Vnext, (const S2*)W, ld, n, ctl, \
                                                                            (const CW*)coefS, hscale);       \
         constexpr size_t SMEM = su_smem_bytes<NF, PW, P>(ROWS);                                             \
-        static bool attr = false;                                                                           \
-        if (!attr) {                                                                                        \
-            cudaFuncSetAttribute(shift_tile_kernel<P, PW, NF, ROWS>,                                        \
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);                    \
-            attr = true;                                                                                    \
-        }                                                                                                   \
+        static std::atomic<unsigned long long> devs{0};                                                     \
+        max_dyn_smem_once(shift_tile_kernel<P, PW, NF, ROWS>, (int)SMEM, devs);                             \
         const unsigned g = (unsigned)(((n + ROWS - 1) / ROWS) * (size_t)s);                                 \
         shift_tile_kernel<P, PW, NF, ROWS><<<g, ROWS / su_rpt(NF, PW), SMEM, st>>>(                                          \
             (const S2*)Vnext, (const S2*)Vk, ld, (W2*)Pp, (W2*)X, ldw, n, s, m, ctl, (const CW*)coefU,      \

@@ -27,12 +27,29 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace dsbcg {
 
 // PDD: double-float ("FP32 pair") fields for the true-residual loop of the
 // reduced-precision solves (see the dd type below); never a storage
 // precision of the Krylov basis.
 enum Prec { P64 = 0, P32 = 1, PBF16 = 2, PF16 = 3, PDD = 4 };
+
+// Raise a kernel's dynamic shared-memory limit once per device (the
+// attribute belongs to the current device); `devs` records the devices done.
+template <class F>
+inline void max_dyn_smem_once(F* func, int bytes, std::atomic<unsigned long long>& devs) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    const unsigned long long bit = (dev >= 0 && dev < 64) ? (1ull << dev) : 0ull;
+    if (bit && (devs.load() & bit)) return;
+    cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    devs.fetch_or(bit);
+}
 
 constexpr int M_MAX = 32;      // largest block width (right-hand sides in a block)
 constexpr int S_MAX = 64;      // largest number of shifts

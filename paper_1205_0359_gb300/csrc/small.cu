@@ -726,6 +726,11 @@ SmallStateT<T>* as_state(SmallState* ss) { return reinterpret_cast<SmallStateT<T
 void launch_small_init(SmallState* ss, Ctl* ctl, const double2* G0, const double* ref, int m, int s, double dtol,
                        int sfp64, cudaStream_t st) {
     size_t sm = 4 * (size_t)m * m * sizeof(double2) + M_MAX * sizeof(int) + 2 * M_MAX * sizeof(double);
+    // above 48 KB from m = 28 on
+    const int sm_max = (int)(4 * (size_t)M_MAX * M_MAX * sizeof(double2) + M_MAX * sizeof(int) + 2 * M_MAX * sizeof(double));
+    static std::atomic<unsigned long long> devs64{0}, devsdd{0};
+    max_dyn_smem_once(small_init_kernel<double2>, sm_max, devs64);
+    max_dyn_smem_once(small_init_kernel<ddc>, sm_max, devsdd);
     if (sfp64)
         small_init_kernel<double2><<<1, WS, sm, st>>>(as_state<double2>(ss), ctl, G0, ref, m, s, dtol);
     else
@@ -747,14 +752,9 @@ void launch_small_step(SmallState* ss, Ctl* ctl, const double* partials, int nbl
                        void* coefS_w, void* coefU_w, void* coefL_w, int* active, int* conv_step, double* res_out,
                        cudaStream_t st) {
     const int MM = m;                  // block widths never exceed the initial width m
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(small_step_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)step_smem(M_MAX));
-        cudaFuncSetAttribute(small_step_kernel<ddc>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)step_smem(M_MAX));
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> devs64{0}, devsdd{0};
+    max_dyn_smem_once(small_step_kernel<double2>, (int)step_smem(M_MAX), devs64);
+    max_dyn_smem_once(small_step_kernel<ddc>, (int)step_smem(M_MAX), devsdd);
     if (sfp64)
         small_step_kernel<double2><<<s, NT, step_smem(MM), st>>>(as_state<double2>(ss), ctl, partials, nblk, m, dtol,
                                                                  sigma_dev, target_dev, freeze, wprec, coefS_w,

@@ -196,16 +196,18 @@ def test_paper_comparison_special_cases():
     assert mv["CG"] == max(mv.values()), mv
 
 
+@pytest.mark.parametrize("m", [20, 32])
 @pytest.mark.parametrize("storage", ["fp64", "fp32"])
-def test_wide_block_against_dense_lu(storage):
-    """m = 20 right-hand sides: block widths above 16 take the untiled Gram
-    kernel; solutions against dense LU on 4^4."""
+def test_wide_block_against_dense_lu(storage, m):
+    """m = 20 and 32 right-hand sides (the largest block): widths above 16
+    take the untiled Gram kernel, and from 28 on the initial QR needs more
+    than 48 KB of shared memory; solutions against dense LU on 4^4."""
     dims = (4, 4, 4, 4)
     rng = np.random.Generator(np.random.PCG64(77))
     U = synth.su3_links(dims, 0.3, rng)
     kappa = 0.12
     n = 12 * synth.volume(dims)
-    B = synth.gaussian_rhs(n, 20, rng)
+    B = synth.gaussian_rhs(n, m, rng)
     sigma = np.array([1e-2, 1.0])
     Ad = W.dense_A(U, kappa, dims)
     Xd = dense_solve(Ad, B, sigma)
