@@ -92,6 +92,11 @@ typedef struct {
                                accumulated solutions and the m x m coefficient work in
                                double-float arithmetic (DSBCG_PREC_DF32) on the FP32
                                pipes; 1: all of them in IEEE FP64, as with FP64 storage */
+    int x0;                 /* 1: X's input is an initial guess X_0 for every system (a
+                               resumed solve): the joint block solve is skipped and
+                               each shift is restarted from its own true residual
+                               b_i - (sigma_j + A) x0_ij; 0 (default): X's input is
+                               ignored and X_0 = 0 */
 } dsbcg_params;
 
 typedef struct {
@@ -154,7 +159,8 @@ dsbcg_status dsbcg_update_gauge(dsbcg_ctx* ctx, const void* gauge);
  *   s:     number of shifts, 1 <= s <= 64
  *   sigma: HOST double[s], each >= 0
  *   tol:   target ||b_i - (sigma_j + A) x_ij|| <= tol ||b_i|| for every (i, j)
- *   X:     device or host complex128 [s][m][n]; output (its input value is ignored)
+ *   X:     device or host complex128 [s][m][n]; output (its input value is the
+ *          initial guess with params->x0, otherwise ignored)
  *   params: NULL for defaults
  *   stats: NULL or caller-owned
  * Returns DSBCG_OK when every true relative residual meets tol,

@@ -652,6 +652,7 @@ void dsbcg_params_default(dsbcg_params* p) {
     p->freeze_converged = 1;
     p->refine = 1;
     p->fp64_residuals = 0;
+    p->x0 = 0;
 }
 
 const char* dsbcg_error_string(dsbcg_status s) {
@@ -885,6 +886,31 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
         }
     }
     if (hflag) return DSBCG_ERR_NONFINITE;
+    // --- initial guess (a resumed solve): X's input, packed shift by shift
+    // into the high-precision X_j (the norms above were taken with X = 0)
+    if (prm.x0) {
+        const void* xin_map = x_dev ? nullptr : mapped_host_ptr(X);
+        CK(cudaMemsetAsync(w.flag, 0, sizeof(int), c->st));
+        for (int j = 0; j < s; ++j) {
+            const double2* src = nullptr;
+            if (x_dev) {
+                src = (const double2*)X + (size_t)j * m * n;
+            } else if (xin_map) {
+                src = (const double2*)xin_map + (size_t)j * m * n;
+            } else {
+                CK(cudaMemcpyAsync(w.T64a, (const double2*)X + (size_t)j * m * n, (size_t)m * n * sizeof(double2),
+                                   cudaMemcpyHostToDevice, c->st));
+                src = w.T64a;
+            }
+            Prof p(c, DSBCG_KCLASS_OTHER, 2);
+            launch_check_finite(src, (size_t)m * n, w.flag, c->st);
+            pack_any(c, hp, w.X64 + (size_t)j * m * ld, src, m);
+        }
+        int xflag = 0;
+        CK(cudaMemcpyAsync(&xflag, w.flag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        if (xflag) return DSBCG_ERR_NONFINITE;
+    }
 
     std::vector<double> rel((size_t)s * m, 0.0);
     std::vector<int> conv((size_t)s * m, -1);
@@ -905,8 +931,9 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
     };
     const double drop = mixed ? std::max(prm.restart_drop, 1e-12) : 0.0;
 
-    // --- joint inner solve on B for all shifts
-    {
+    // --- joint inner solve on B for all shifts (not with an initial guess:
+    // the shifts' residuals then differ, and each is restarted on its own)
+    if (!prm.x0) {
         std::vector<double> tg((size_t)s * m);
         for (int j = 0; j < s; ++j)
             for (int i = 0; i < m; ++i) tg[(size_t)j * m + i] = std::max(drop * bn[i], 0.5 * tol * bn[i]);

@@ -42,7 +42,7 @@ class Params(ctypes.Structure):
                 ("max_block_steps", ctypes.c_int), ("max_restarts", ctypes.c_int),
                 ("restart_drop", ctypes.c_double), ("poll_every", ctypes.c_int),
                 ("freeze_converged", ctypes.c_int), ("refine", ctypes.c_int),
-                ("fp64_residuals", ctypes.c_int)]
+                ("fp64_residuals", ctypes.c_int), ("x0", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -167,10 +167,11 @@ class Context:
 
     def solve(self, B, sigma, tol, storage="fp32", out=None, dtol=0.0, max_block_steps=None,
               max_restarts=None, restart_drop=None, poll_every=None, freeze=True, refine=True,
-              fp64_residuals=False, raise_on_error=True):
+              fp64_residuals=False, x0=None, raise_on_error=True):
         """X (s, m, n) complex128 for (sigma_j + A) X_j = B; B (m, n) complex128.
 
         B and out may live on the GPU or on the host; the result has B's device.
+        x0: optional initial guess (s, m, n) to resume from (dsbcg_params.x0).
         Returns (X, stats dict)."""
         B = _as_c128(B)
         m = B.shape[0]
@@ -196,6 +197,14 @@ class Context:
         p.freeze_converged = int(bool(freeze))
         p.refine = int(bool(refine))
         p.fp64_residuals = int(bool(fp64_residuals))
+        if x0 is not None:
+            # initial guess (s, m, n): the solve resumes from it, in place in `out`
+            if isinstance(out, torch.Tensor):
+                if x0 is not out:
+                    out.copy_(torch.as_tensor(x0).reshape(out.shape))
+            else:
+                out[...] = np.asarray(x0).reshape(out.shape)
+            p.x0 = 1
         rel = np.zeros((s, m), dtype=np.float64)
         conv = np.zeros((s, m), dtype=np.int32)
         st = Stats()

@@ -219,3 +219,29 @@ def test_wide_block_against_dense_lu(storage, m):
         assert _relerr(X.cpu().numpy(), Xd).max() <= 1e-7
     finally:
         ctx.close()
+
+
+def test_resume_from_initial_guess(w1):
+    """dsbcg_params.x0: a solve resumed from X_0.  From the exact solution no
+    block step is needed; a loose solve resumed at a tight tolerance reaches
+    it and agrees with dense LU."""
+    wl, Ad, Xd, ctx = w1
+    B = torch.from_numpy(wl["B"]).to(DEV)
+    X, st = ctx.solve(B, wl["sigma"], 1e-10, storage="fp32", x0=torch.from_numpy(Xd).to(DEV))
+    assert st["code"] == 0 and st["block_steps"] == 0 and st["restarts"] == 0
+    assert _relerr(X.cpu().numpy(), Xd).max() <= 1e-12
+    X1, st1 = ctx.solve(B, wl["sigma"], 1e-5, storage="fp32", refine=False, raise_on_error=False)
+    X2, st2 = ctx.solve(B, wl["sigma"], 1e-10, storage="fp32", x0=X1)
+    assert st2["code"] == 0 and st2["true_relres"].max() <= 1e-10
+    assert _relerr(X2.cpu().numpy(), Xd).max() <= 1e-7
+
+
+def test_restart_cap_reports_not_converged(w1):
+    """FP32 storage cannot reach 1e-10 without restarts: with max_restarts = 0
+    the solve reports NOT_CONVERGED and still returns finite iterates."""
+    wl, Ad, Xd, ctx = w1
+    X, st = ctx.solve(torch.from_numpy(wl["B"]).to(DEV), wl["sigma"], 1e-10, storage="fp32", max_restarts=0,
+                      raise_on_error=False)
+    assert st["code"] == 1 and st["restarts"] == 0
+    assert st["true_relres"].max() > 1e-10
+    assert bool(torch.isfinite(X).all())
