@@ -19,12 +19,13 @@
  *   antiperiodic in time when t_antiperiodic != 0.  D^H = gamma_5 D gamma_5.
  *
  * Pointers: "device or host" arguments may point to device memory or to host
- * memory (pageable or pinned); the library detects which and copies host
- * data in and out on the context's stream (results bound for pinned host
- * memory that is mapped into the device address space are written there
- * directly by the output kernel).  The caller owns every buffer it
- * passes; the library never frees them.  A context owns its workspace and its
- * packed copies of the gauge field.
+ * memory (pageable or pinned); the library detects which.  Page-locked host
+ * memory mapped into the device address space is read and written in place
+ * by the library's kernels; other host memory is staged through device
+ * buffers on the context's stream.  The caller owns every buffer it passes;
+ * the library never frees them.  A context owns its workspace (including
+ * the streams of its concurrent restarts) and its packed copies of the gauge
+ * field.
  *
  * Errors: every call returns a dsbcg_status; nothing is thrown across the
  * ABI.  After DSBCG_ERR_CUDA the context should be destroyed.
