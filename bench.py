@@ -355,6 +355,8 @@ def run_ours(args):
 
     if rank == 0 and not args.no_compare:
         line["comparison"] = run_comparison(dev, stream)
+    if rank == 0 and args.sweeps:
+        line["sweeps"] = run_sweeps(dev, stream)
 
     fp64_mvms = None
     if rank == 0 and not args.no_fp64:
@@ -434,6 +436,61 @@ def run_comparison(dev, stream, name="cmp_16x16x16x16", storage="fp64", dims=Non
             "algorithms": out}
 
 
+def run_sweeps(dev, stream, storage="fp64"):
+    """The paper's two sweeps (Sec. 4, Figs. 2 and 3), DSBlockCG against
+    shifted CG (one solve per right-hand side with all shifts) on the same
+    kernels: 16^4 with m = 4 and a growing number of shifts spread over
+    1e-6..1e-1, and 12^4 with s = 10 shifts and a growing number of
+    right-hand sides.  Each point: mvms and GPU time of both, and the ratios
+    DSBlockCG / shifted CG the figures plot."""
+    import dataclasses
+    import torch
+    from paper_1205_0359_gb300 import dsbcg, synth
+
+    def timed(ctx, B, sig, tol):
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st = ctx.solve(B, sig, tol, storage=storage)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return st, e0.elapsed_time(e1)
+
+    def point(ctx, B, sig, tol):
+        ctx.solve(B, sig, tol, storage=storage)                        # warm-up, this shape
+        st, t_dsb = timed(ctx, B, sig, tol)
+        mv_sh, t_sh = 0, 0.0
+        ctx.solve(B[0:1].contiguous(), sig, tol, storage=storage)
+        for i in range(B.shape[0]):
+            st1, t1 = timed(ctx, B[i:i + 1].contiguous(), sig, tol)
+            mv_sh += st1["mvms"]
+            t_sh += t1
+        return {"dsb_mvms": int(st["mvms"]), "shifted_mvms": int(mv_sh), "dsb_ms": round(t_dsb, 2),
+                "shifted_ms": round(t_sh, 2), "mvms_ratio": round(st["mvms"] / mv_sh, 3),
+                "time_ratio": round(t_dsb / t_sh, 3)}
+
+    base = synth.WORKLOADS["cmp_16x16x16x16"]
+    out = {"shift_sweep": {}, "rhs_sweep": {}}
+    d = synth.make_workload(base, m=4)
+    ctx = dsbcg.Context(d["dims"], torch.from_numpy(d["U"]).to(dev), d["kappa"], stream=stream)
+    B = torch.from_numpy(d["B"]).to(dev)
+    for s in (1, 2, 4, 7, 10):
+        sig = synth.log_shifts(1e-6, 1e-1, s) if s > 1 else np.array([1e-6])
+        out["shift_sweep"][str(s)] = point(ctx, B, sig, base.tol)
+    ctx.close()
+    wl12 = dataclasses.replace(base, name="cmp_12x12x12x12", dims=(12, 12, 12, 12), m=12, s=10,
+                               shifts=tuple(synth.log_shifts(1e-6, 1e-1, 10)))
+    d = synth.make_workload(wl12)
+    ctx = dsbcg.Context(d["dims"], torch.from_numpy(d["U"]).to(dev), d["kappa"], stream=stream)
+    Ball = torch.from_numpy(d["B"]).to(dev)
+    for m in (1, 2, 4, 6, 8, 12):
+        out["rhs_sweep"][str(m)] = point(ctx, Ball[:m].contiguous(), np.asarray(d["sigma"]), base.tol)
+    ctx.close()
+    out["workload"] = (f"16^4 (m = 4, s = 1..10) and 12^4 (s = 10, m = 1..12), kappa {base.kappa}, "
+                       f"shifts 1e-6..1e-1, tol {base.tol:.0e}, {storage} storage")
+    return out
+
+
 def run_reference(args):
     """The FP64 CPU oracle on the host cores, as the reference implementation."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -477,6 +534,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-force", action="store_true", help="skip the gauge-force timing")
+    ap.add_argument("--sweeps", action="store_true",
+                    help="also run the paper's shift and right-hand-side sweeps (DSBlockCG vs shifted CG)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the paper's algorithm comparison (CG, block CG, shifted CG, DSBlockCG)")
     ap.add_argument("--cpu-vectors", type=int, default=2)
