@@ -36,6 +36,12 @@
 #include "../../include/dsbcg.h"
 #include "kernels.h"
 
+// NVTX ranges (header-only NVTX 3; no-ops unless a profiler attaches)
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+#define DSBCG_HAVE_NVTX 1
+#endif
+
 using namespace dsbcg;
 
 namespace {
@@ -124,6 +130,24 @@ struct dsbcg_ctx {
 };
 
 namespace {
+
+// one named NVTX range for the lifetime of the object (host thread)
+struct Range {
+    explicit Range(const char* name) {
+#ifdef DSBCG_HAVE_NVTX
+        nvtxRangePushA(name);
+#else
+        (void)name;
+#endif
+    }
+    ~Range() {
+#ifdef DSBCG_HAVE_NVTX
+        nvtxRangePop();
+#endif
+    }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 #define CK(x)                                              \
     do {                                                   \
@@ -439,6 +463,7 @@ void apply_Ahp(dsbcg_ctx* c, int hp, void* out, const void* in, void* tmp, int n
 // into h_out (host)
 dsbcg_status true_residual(dsbcg_ctx* c, int hp, double2* r, const double2* b, const double2* x, int m,
                            double sigma, double* h_out) {
+    Range r_res("true residual");
     auto& w = c->ws;
     apply_Ahp(c, hp, w.T64b, x, w.T64a, m);
     {
@@ -816,6 +841,7 @@ dsbcg_status dsbcg_apply(dsbcg_ctx* c, int op, int storage, int m, const void* i
 
 dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double* sigma, double tol,
                          const dsbcg_params* params, void* X, dsbcg_stats* stats) {
+    Range r_solve("dsbcg_solve");
     auto t0 = std::chrono::steady_clock::now();
     if (!c || !B || !X || !sigma || m < 1 || m > M_MAX || s < 1 || s > S_MAX) return DSBCG_ERR_ARG;
     if (!(tol >= 0.0) || !isfinite(tol)) return DSBCG_ERR_ARG;
@@ -934,6 +960,7 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
     // --- joint inner solve on B for all shifts (not with an initial guess:
     // the shifts' residuals then differ, and each is restarted on its own)
     if (!prm.x0) {
+        Range r_joint("joint block solve");
         std::vector<double> tg((size_t)s * m);
         for (int j = 0; j < s; ++j)
             for (int i = 0; i < m; ++i) tg[(size_t)j * m + i] = std::max(drop * bn[i], 0.5 * tol * bn[i]);
@@ -1050,6 +1077,7 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
             lane_j[li] = j;
         }
     };
+    Range r_ref("per-shift restarts");
     CKS(feed());
     for (;;) {
         bool busy = false;
