@@ -46,7 +46,8 @@ class NotHPD(ArithmeticError):
 
 
 def dsbcg(apply_A, B, sigma, tol, dtol=1e-12, max_vectors=None, freeze=True,
-          check_every=None, keep_basis=False, stop_after_vectors=None):
+          check_every=None, keep_basis=False, stop_after_vectors=None,
+          estimate=False):
     """Solve (sigma_j I + A) X_j = B for all shifts with one band Lanczos run.
 
     apply_A : callable mapping an (n,) or (k, n) complex array to A times it
@@ -56,6 +57,11 @@ def dsbcg(apply_A, B, sigma, tol, dtol=1e-12, max_vectors=None, freeze=True,
     stop_after_vectors : stop after exactly this many Lanczos vectors (no
               convergence test, no final residual pass); used to compare
               against Eq. 3.2 at fixed k and to time a bounded sample.
+    estimate : also return info["est_relres"], shape (s, m): the residual
+              norms of the Galerkin iterates after the last vector, computed
+              without a product with A (Sec. 3, R = W C; see residual_estimate
+              below).  Meaningful with freeze=False: a frozen system's
+              iterate is no longer the Galerkin iterate.
 
     Returns (X, info) with X of shape (s, m, n).
     """
@@ -183,6 +189,9 @@ def dsbcg(apply_A, B, sigma, tol, dtol=1e-12, max_vectors=None, freeze=True,
                 converged = True
                 break
 
+    est = None
+    if estimate:
+        est = residual_estimate(pending, Lrow, dval, urow, len(V), s, m, bnorm)
     if not converged and stop_after_vectors is None:
         # final explicit residuals of every system (frozen ones included)
         was_active = active.copy()
@@ -192,6 +201,8 @@ def dsbcg(apply_A, B, sigma, tol, dtol=1e-12, max_vectors=None, freeze=True,
         active[:] = was_active
     info = dict(nvec=len(V), deflations=deflations, deflated_at=deflated_at,
                 relres=relres, converged=converged, invariant=not pending)
+    if est is not None:
+        info["est_relres"] = est
     if keep_basis:
         k = len(V)
         Tm = np.zeros((k, k), dtype=np.complex128)
@@ -205,6 +216,57 @@ def dsbcg(apply_A, B, sigma, tol, dtol=1e-12, max_vectors=None, freeze=True,
                 Rm[r, c] = val
         info.update(V=np.array(V), T=Tm, rho=Rm)
     return X, info
+
+
+def residual_estimate(pending, Lrow, dval, urow, k, s, m, bnorm):
+    """Residual norms of the Galerkin iterates from the recurrences (Sec. 3).
+
+    The paper states that R = B - (sigma + A) X is orthogonal to the Lanczos
+    vectors built so far and equals W C with W the next (at most m)
+    orthonormal Lanczos vectors, so that ||r_i|| is the norm of column i of
+    C, obtained from T and its root-free Cholesky factors alone.  In the
+    vector-wise process this reads as follows.  With k vectors built, each
+    pending candidate w is orthogonal to v_1..v_k and
+      * if it came from b_c:   b_c   = V rho[:, c] + w,
+      * if it came from A v_q: A v_q = V T[:, q]   + w,
+    so with y = (sigma + T_k)^{-1} rho_k,
+        r_c = sum_{w from b_c} w  -  sum_{w from A v_q} w * y[q, c].
+    The rows y[q] needed are the last ones; they follow from the stored
+    band of the factorisation by back substitution, L^H y = D^{-1} u
+    (u = L^{-1} rho are the u^(i) of the update formula).  W is an
+    orthonormal basis of the pending candidates (QR), and C = R_factor times
+    the coefficient matrix above.  Deflated candidates were dropped as
+    (numerically) zero, so R = W C holds to the deflation tolerance.
+
+    Returns est[j, c] = ||C_j[:, c]|| / ||b_c||, shape (s, m).
+    """
+    est = np.zeros((s, m))
+    if not pending:
+        return est                      # invariant subspace: exact solution
+    Wp = np.array([c["vec"] for c in pending]).T          # n x m_c
+    _, Rf = np.linalg.qr(Wp)
+    av = [c["origin"][1] for c in pending if c["origin"][0] == "Av"]
+    lo = min(av) if av else k
+    bsafe = np.where(bnorm > 0, bnorm, 1.0)
+    for j in range(s):
+        y = {}
+        for i in range(k - 1, lo - 1, -1):
+            yi = urow[j][i] / dval[j][i]
+            for l in range(i + 1, k):
+                lli = Lrow[j][l].get(i)
+                if lli is not None:
+                    yi = yi - np.conj(lli) * y[l]
+            y[i] = yi
+        coef = np.zeros((len(pending), m), dtype=np.complex128)
+        for r, c in enumerate(pending):
+            kind, idx = c["origin"]
+            if kind == "b":
+                coef[r, idx] = 1.0
+            else:
+                coef[r] = -y[idx]
+        C = Rf @ coef
+        est[j] = np.linalg.norm(C, axis=0) / bsafe
+    return est
 
 
 def galerkin_iterate(A_dense, B, sigma, nblocks):

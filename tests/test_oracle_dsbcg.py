@@ -9,7 +9,12 @@ The oracle's recurrences are checked against
   * exact deflation when b_4 = b_1 + b_2 (Sec. 3: the deflated subspace has
     smaller dimension and the bandwidth of T drops),
   * the structural statements of Sec. 3: orthonormal V, hermitian banded T
-    with semi-bandwidth m, T = V^H A V, B = V rho.
+    with semi-bandwidth m, T = V^H A V, B = V rho,
+  * the residual statement of Sec. 3: R is orthogonal to the Lanczos vectors
+    built so far, and the column norms of C in R = W C (computed from T's
+    factors, no product with A) equal the explicit ||b_i - (sigma_j+A) x_ij||,
+    at vector counts inside a block and after a deflation; for m = 1 they are
+    the textbook CG residual norms.
 """
 import numpy as np
 import pytest
@@ -154,3 +159,57 @@ def test_not_hpd_is_reported(small):
     dims, Ad, B, sigma, Aop = small
     with pytest.raises(NotHPD):
         dsbcg(Aop, B, [-10.0], tol=1e-10)
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 7, 11, 16])
+def test_residual_estimate_matches_explicit(small, k):
+    """||C[:, i]|| = ||r_i|| (Sec. 3), also when k is not a multiple of m."""
+    dims, Ad, B, sigma, Aop = small
+    X, info = dsbcg(Aop, B, sigma, tol=0.0, freeze=False, stop_after_vectors=k, estimate=True)
+    rr = true_relres(Aop, B, sigma, X)
+    assert rr.min() > 1e-4                            # not yet converged: a real test
+    assert np.max(np.abs(info["est_relres"] - rr)) <= 1e-11 * rr.max()
+
+
+def test_residual_estimate_with_deflation(w1):
+    """After b_4 = b_1 + b_2 is dropped, W has fewer columns (Sec. 3)."""
+    wl, Ad, Aop = w1
+    B, sigma = wl["B"], wl["sigma"]
+    for k in (5, 9, 14):
+        X, info = dsbcg(Aop, B, sigma, tol=0.0, freeze=False, stop_after_vectors=k, estimate=True)
+        assert info["deflations"] == 1
+        rr = true_relres(Aop, B, sigma, X)
+        assert np.max(np.abs(info["est_relres"] - rr)) <= 1e-11 * rr.max()
+
+
+def test_residual_orthogonal_to_lanczos_vectors(small):
+    """Galerkin condition V^H (B - (sigma+A) X) = 0 at every vector count."""
+    dims, Ad, B, sigma, Aop = small
+    for k in (2, 5, 10):
+        X, info = dsbcg(Aop, B, sigma, tol=0.0, freeze=False, stop_after_vectors=k, keep_basis=True)
+        V = info["V"]
+        for j, sg in enumerate(sigma):
+            R = B - sg * X[j] - Aop(X[j])
+            proj = V.conj() @ R.T
+            assert np.max(np.abs(proj)) <= 1e-11 * np.max(np.abs(R)), (k, j)
+
+
+def test_residual_estimate_m1_is_cg_residual(small):
+    """m = s = 1: the estimate is ||r_k|| of textbook CG on (sigma + A) x = b."""
+    dims, Ad, B, sigma, Aop = small
+    b = B[0]
+    sg = sigma[2]
+    M = Ad + sg * np.eye(Ad.shape[0])
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    for k in range(1, 8):
+        Mp = M @ p
+        a = np.vdot(r, r).real / np.vdot(p, Mp).real
+        x = x + a * p
+        rn = r - a * Mp
+        p = rn + (np.vdot(rn, rn).real / np.vdot(r, r).real) * p
+        r = rn
+        _, info = dsbcg(Aop, b[None], [sg], tol=0.0, freeze=False, stop_after_vectors=k, estimate=True)
+        want = np.linalg.norm(r) / np.linalg.norm(b)
+        assert abs(info["est_relres"][0, 0] - want) <= 1e-10 * want, k
