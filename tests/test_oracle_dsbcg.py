@@ -5,7 +5,8 @@ The oracle's recurrences are checked against
   * the Galerkin definition X = V (V^H (sigma+A) V)^{-1} V^H B over the block
     Krylov subspace (Eqs. 2.1, 2.2, 3.2), with a basis built by fully
     orthogonalised block Arnoldi, at a fixed number of block steps,
-  * textbook CG iterates for m = s = 1,
+  * textbook CG iterates for m = s = 1, CG per shift for m = 1 (shifted
+    CG), and block CG iterates for s = 1,
   * exact deflation when b_4 = b_1 + b_2 (Sec. 3: the deflated subspace has
     smaller dimension and the bandwidth of T drops),
   * the structural statements of Sec. 3: orthonormal V, hermitian banded T
@@ -213,3 +214,57 @@ def test_residual_estimate_m1_is_cg_residual(small):
         _, info = dsbcg(Aop, b[None], [sg], tol=0.0, freeze=False, stop_after_vectors=k, estimate=True)
         want = np.linalg.norm(r) / np.linalg.norm(b)
         assert abs(info["est_relres"][0, 0] - want) <= 1e-10 * want, k
+
+
+def _cg_iterates(M, b, steps):
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    out = []
+    for _ in range(steps):
+        Mp = M @ p
+        a = np.vdot(r, r).real / np.vdot(p, Mp).real
+        x = x + a * p
+        rn = r - a * Mp
+        p = rn + (np.vdot(rn, rn).real / np.vdot(r, r).real) * p
+        r = rn
+        out.append(x.copy())
+    return out
+
+
+def test_m1_is_shifted_cg(small):
+    """m = 1, s = 4: every shift follows its own textbook CG iterates (the
+    shifted CG of Sec. 1), from one Lanczos run."""
+    dims, Ad, B, sigma, Aop = small
+    b = B[1]
+    I = np.eye(Ad.shape[0])
+    ref = [_cg_iterates(Ad + sg * I, b, 9) for sg in sigma]
+    for k in (1, 4, 9):
+        X, _ = dsbcg(Aop, b[None], sigma, tol=0.0, freeze=False, stop_after_vectors=k)
+        for j in range(len(sigma)):
+            x = ref[j][k - 1]
+            assert np.linalg.norm(X[j, 0] - x) <= 1e-10 * np.linalg.norm(x), (k, j)
+
+
+def test_s1_is_block_cg(small):
+    """s = 1: the iterates of O'Leary's block CG at every block step (no
+    dependent right-hand sides here, so no deflation)."""
+    dims, Ad, B, sigma, Aop = small
+    sg = sigma[1]
+    M = Ad + sg * np.eye(Ad.shape[0])
+    m = B.shape[0]
+    Xb = np.zeros((Ad.shape[0], m), dtype=np.complex128)
+    R = B.T.copy()
+    P = R.copy()
+    for k in range(1, 6):
+        MP = M @ P
+        alpha = np.linalg.solve(P.conj().T @ MP, R.conj().T @ R)
+        Xb = Xb + P @ alpha
+        Rn = R - MP @ alpha
+        beta = np.linalg.solve(R.conj().T @ R, Rn.conj().T @ Rn)
+        P = Rn + P @ beta
+        R = Rn
+        X, info = dsbcg(Aop, B, [sg], tol=0.0, freeze=False, stop_after_vectors=m * k)
+        assert info["deflations"] == 0
+        err = np.linalg.norm(X[0] - Xb.T, axis=1) / np.linalg.norm(Xb.T, axis=1)
+        assert err.max() <= 1e-9, (k, err.max())
