@@ -16,8 +16,13 @@ Modules
   dsbcg   -- DSBlockCG: hermitian band Lanczos with deflation + per-shift
              root-free Cholesky updates of the iterates (Sec. 3, Eqs. 3.1-3.2)
   force   -- gradients of the RHMC-style loss w.r.t. B, sigma_j and the links
+  evenodd -- even-odd Schur complement Dhat = 1 - kappa^2 H_oe H_eo of D and
+             Ahat = Dhat^H Dhat on the odd sites (a preconditioned variant,
+             not the paper's operator)
 
 Parity status: every function here is pinned by tests in tests/test_oracle_*.py
 (dense LU, free-field closed form, gamma5-hermiticity, Galerkin definition,
-textbook CG, deflation, finite differences).
+textbook, shifted and block CG, deflation, residual estimate, finite
+differences, dense Schur complement and the paired spectrum of the hopping
+term).
 """

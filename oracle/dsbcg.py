@@ -269,6 +269,21 @@ def residual_estimate(pending, Lrow, dval, urow, k, s, m, bnorm):
     return est
 
 
+def rational_combination(B, X, alpha0, alpha):
+    """Y = alpha_0 B + sum_j alpha_j X_j, shape (m, n).
+
+    With X_j = (sigma_j I + A)^{-1} B this is r(A) B for the partial fraction
+    r(x) = alpha_0 + sum_j alpha_j / (x + sigma_j): the form in which a
+    rational approximation of A^nu turns into the shifted systems of Eq. 1.1
+    (Sec. 1, the RHMC application).
+    """
+    B = np.asarray(B, dtype=np.complex128)
+    Y = alpha0 * B
+    for j, a in enumerate(np.atleast_1d(alpha)):
+        Y = Y + a * X[j]
+    return Y
+
+
 def galerkin_iterate(A_dense, B, sigma, nblocks):
     """Definition of the block Galerkin iterate (Eqs. 2.2 and 3.2).
 

@@ -15,13 +15,17 @@ The oracle's recurrences are checked against
     built so far, and the column norms of C in R = W C (computed from T's
     factors, no product with A) equal the explicit ||b_i - (sigma_j+A) x_ij||,
     at vector counts inside a block and after a deflation; for m = 1 they are
-    the textbook CG residual norms.
+    the textbook CG residual norms,
+  * the rational combination alpha_0 B + sum_j alpha_j X_j (Sec. 1) against
+    r(A) B through A's eigendecomposition, a closed partial fraction, and a
+    quadrature approximation of A^{-1/2} within its spectral error bound.
 """
 import numpy as np
 import pytest
 
 from oracle import wilson as W
-from oracle.dsbcg import NotHPD, dense_solve, dsbcg, galerkin_iterate, true_relres
+from oracle.dsbcg import (NotHPD, dense_solve, dsbcg, galerkin_iterate, rational_combination,
+                          true_relres)
 from paper_1205_0359_gb300 import synth
 
 
@@ -268,3 +272,53 @@ def test_s1_is_block_cg(small):
         assert info["deflations"] == 0
         err = np.linalg.norm(X[0] - Xb.T, axis=1) / np.linalg.norm(Xb.T, axis=1)
         assert err.max() <= 1e-9, (k, err.max())
+
+
+def test_rational_combination_is_r_of_A(small):
+    """alpha_0 B + sum_j alpha_j X_j = Q r(Lambda) Q^H B (Sec. 1), with the
+    iterates of one DSBlockCG run and r evaluated on A's eigenvalues."""
+    dims, Ad, B, sigma, Aop = small
+    X, info = dsbcg(Aop, B, sigma, tol=1e-13)
+    assert info["converged"]
+    alpha0, alpha = 0.3, np.array([0.7, -0.2, 1.5, 0.05])
+    Y = rational_combination(B, X, alpha0, alpha)
+    lam, Q = np.linalg.eigh(Ad)
+    r = alpha0 + sum(a / (lam + sg) for a, sg in zip(alpha, sigma))
+    Yd = (Q @ (r[:, None] * (Q.conj().T @ B.T))).T
+    assert np.linalg.norm(Y - Yd) <= 1e-10 * np.linalg.norm(Yd)
+
+
+def test_rational_combination_partial_fraction(small):
+    """1/((x+a)(x+b)) = (1/(x+a) - 1/(x+b)) / (b-a): the combination equals a
+    solve with the product (A+a)(A+b)."""
+    dims, Ad, B, sigma, Aop = small
+    a, b = 0.01, 0.5
+    X, _ = dsbcg(Aop, B, [a, b], tol=1e-13)
+    Y = rational_combination(B, X, 0.0, [1.0 / (b - a), -1.0 / (b - a)])
+    I = np.eye(Ad.shape[0])
+    Yd = np.linalg.solve((Ad + a * I) @ (Ad + b * I), B.T).T
+    assert np.linalg.norm(Y - Yd) <= 1e-9 * np.linalg.norm(Yd)
+
+
+def test_rational_inverse_square_root(small):
+    """nu = -1/2: the substitution t = e^u in x^{-1/2} = (2/pi) int_0^inf
+    dt / (t^2 + x) and the trapezoidal rule give shifts sigma_k = e^{2 u_k}
+    and weights alpha_k = (2 h / pi) e^{u_k}.  A is hermitian, so
+    ||r(A) b - A^{-1/2} b|| <= max over A's eigenvalues |r - lambda^{-1/2}|
+    times ||b||."""
+    dims, Ad, B, sigma, Aop = small
+    lam, Q = np.linalg.eigh(Ad)
+    assert lam.min() > 0
+    h = 0.35
+    u = np.arange(-40, 41) * h
+    sig, alpha = np.exp(2 * u), (2 * h / np.pi) * np.exp(u)
+    X, info = dsbcg(Aop, B, sig, tol=1e-13)
+    assert info["converged"]
+    Y = rational_combination(B, X, 0.0, alpha)
+    r = sum(a / (lam + s_) for a, s_ in zip(alpha, sig))
+    bound = np.max(np.abs(r - lam ** -0.5))
+    assert bound < 1e-5                                # the rule is accurate here
+    Yd = (Q @ ((lam ** -0.5)[:, None] * (Q.conj().T @ B.T))).T
+    for i in range(B.shape[0]):
+        err = np.linalg.norm(Y[i] - Yd[i])
+        assert err <= bound * np.linalg.norm(B[i]) + 1e-9 * np.linalg.norm(Yd[i]), i
