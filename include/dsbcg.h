@@ -140,7 +140,11 @@ void dsbcg_params_default(dsbcg_params* p);
 dsbcg_status dsbcg_create(dsbcg_ctx** out, const int dims[4], const void* gauge,
                           double kappa, int t_antiperiodic, void* stream);
 
-/* Replace the gauge field of an existing context (same dims). */
+/* Replace the gauge field of an existing context (same dims).  The new field
+ * is checked for NaN/Inf (DSBCG_ERR_NONFINITE) and packed again for every
+ * precision on first use.  After any failed update the context holds no
+ * gauge field: dsbcg_solve, dsbcg_apply, dsbcg_apply_static and dsbcg_force
+ * return DSBCG_ERR_ARG until an update succeeds. */
 dsbcg_status dsbcg_update_gauge(dsbcg_ctx* ctx, const void* gauge);
 
 /* Solve (sigma_j I + A) X_j = B for j = 1..s with one block Lanczos process

@@ -95,6 +95,7 @@ struct dsbcg_ctx {
     double2* gauge64 = nullptr;          // canonical copy of the links (device)
     void* links[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // per Prec (PDD: double-float)
     float hscale = 1.f;
+    bool gauge_ok = false;               // gauge64 holds a checked field and links[] were packed from it
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<KEvent> ev_live;
@@ -727,6 +728,16 @@ dsbcg_status dsbcg_create(dsbcg_ctx** out, const int dims[4], const void* gauge,
 
 dsbcg_status dsbcg_update_gauge(dsbcg_ctx* c, const void* gauge) {
     if (!c || !gauge) return DSBCG_ERR_ARG;
+    // From here until the new field has been checked and packed the context
+    // holds no usable field: the old packed links go first, so that no
+    // precision keeps links of the old field while gauge64 holds the new one.
+    c->gauge_ok = false;
+    for (int p = 0; p < 5; ++p) {
+        if (c->links[p]) {
+            cudaFree(c->links[p]);
+            c->links[p] = nullptr;
+        }
+    }
     const size_t bytes = c->V * 36 * sizeof(double2);
     if (!c->gauge64) CK(cudaMalloc((void**)&c->gauge64, bytes));
     CK(cudaMemcpyAsync(c->gauge64, gauge, bytes, is_device_ptr(gauge) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -737,16 +748,12 @@ dsbcg_status dsbcg_update_gauge(dsbcg_ctx* c, const void* gauge) {
     launch_check_finite(c->gauge64, c->V * 36, flag, c->st);
     int h = 0;
     cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, c->st);
-    CK(cudaStreamSynchronize(c->st));
+    const cudaError_t e = cudaStreamSynchronize(c->st);
     cudaFree(flag);
+    CK(e);
     if (h) return DSBCG_ERR_NONFINITE;
-    for (int p = 0; p < 5; ++p) {
-        if (c->links[p]) {
-            cudaFree(c->links[p]);
-            c->links[p] = nullptr;
-        }
-    }
     CKS(ensure_links(c, P64));
+    c->gauge_ok = true;
     return DSBCG_OK;
 }
 
@@ -787,6 +794,7 @@ dsbcg_status dsbcg_read_profile(dsbcg_ctx* c, double kernel_ms[8], long long ker
 dsbcg_status dsbcg_apply(dsbcg_ctx* c, int op, int storage, int m, const void* in, void* out) {
     if (!c || !in || !out || m < 1 || m > 4096 || op < 0 || op > 2 || storage < 0 || storage > PDD)
         return DSBCG_ERR_ARG;
+    if (!c->gauge_ok) return DSBCG_ERR_ARG;
     CKS(ensure_links(c, storage));
     const size_t n = c->n, ld = hp_ld(c, storage);
     const size_t fb = prec_elem_bytes(storage) * c->ld;
@@ -844,6 +852,7 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
     Range r_solve("dsbcg_solve");
     auto t0 = std::chrono::steady_clock::now();
     if (!c || !B || !X || !sigma || m < 1 || m > M_MAX || s < 1 || s > S_MAX) return DSBCG_ERR_ARG;
+    if (!c->gauge_ok) return DSBCG_ERR_ARG;
     if (!(tol >= 0.0) || !isfinite(tol)) return DSBCG_ERR_ARG;
     for (int j = 0; j < s; ++j)
         if (!(sigma[j] >= 0.0) || !isfinite(sigma[j])) return DSBCG_ERR_ARG;
@@ -1157,6 +1166,7 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
 dsbcg_status dsbcg_force(dsbcg_ctx* c, int m, int s, const void* X, const void* Lambda, const double* weights,
                          int storage, void* dU) {
     if (!c || !X || !Lambda || !dU || m < 1 || s < 1 || (size_t)m * s > 4096) return DSBCG_ERR_ARG;
+    if (!c->gauge_ok) return DSBCG_ERR_ARG;
     if (storage != P64 && storage != P32) return DSBCG_ERR_UNSUPPORTED;
     CKS(ensure_links(c, storage));
     const size_t n = c->n, ld = c->ld, V = c->V;
@@ -1255,6 +1265,7 @@ dsbcg_status static_scratch_address(void** out) {
 
 extern "C" dsbcg_status dsbcg_apply_static(dsbcg_ctx* c, int op, int storage, int m, const void* in, void* out) {
     if (!c || !in || !out || m < 1 || op < 0 || op > 2 || storage < 0 || storage > PDD) return DSBCG_ERR_ARG;
+    if (!c->gauge_ok) return DSBCG_ERR_ARG;
     if (!is_device_ptr(in) || !is_device_ptr(out)) return DSBCG_ERR_ARG;
     if (!c->links[storage]) return DSBCG_ERR_UNSUPPORTED;
     const size_t ld = hp_ld(c, storage);
