@@ -69,9 +69,11 @@ def test_fd_gradients_2x2x2x2():
         assert abs(fd - an) <= 1e-5 * max(abs(an), 1e-8)
 
 
-def test_fd_link_gradient_general_adjoint_2x2x2x2():
-    """General incoming gradient: L = sum_j Re tr(C_j^H X_j) for fixed C_j;
-    then Lambda_j = (sigma_j + A)^{-1} C_j and dL/dU = -(kappa...) via F."""
+@pytest.mark.parametrize("weights", [None, (0.3, 1.7)])
+def test_fd_link_gradient_general_adjoint_2x2x2x2(weights):
+    """General incoming gradient: L = sum_j w_j Re tr(C_j^H X_j) for fixed
+    C_j; then Lambda_j = (sigma_j + A)^{-1} C_j and link_gradient with the
+    per-shift weights w_j (default 1) gives dL/dU."""
     dims = (2, 2, 2, 2)
     rng = np.random.Generator(np.random.PCG64(405))
     U = synth.su3_links(dims, 0.5, rng)
@@ -80,16 +82,17 @@ def test_fd_link_gradient_general_adjoint_2x2x2x2():
     B = synth.gaussian_rhs(n, 2, rng)
     C = _cplx(rng, (2, 2, n))
     sigma = np.array([0.05, 0.5])
+    wt = np.ones(2) if weights is None else np.asarray(weights)
 
     def loss(Uv):
         X = dense_solve(W.dense_A(Uv, kappa, dims), B, sigma)
-        return sum(_re_inner(C[j], X[j]) for j in range(2))
+        return sum(wt[j] * _re_inner(C[j], X[j]) for j in range(2))
 
     Ad = W.dense_A(U, kappa, dims)
     X = dense_solve(Ad, B, sigma)
     Lam = np.array([np.linalg.solve(Ad + sigma[j] * np.eye(n), C[j].T).T for j in range(2)])
     # dL = -Re tr(Lam^H dA X) -> the sign is carried by link_gradient's convention
-    gU = link_gradient(U, kappa, dims, X, Lam)
+    gU = link_gradient(U, kappa, dims, X, Lam, weights)
     h = 1e-6
     for _ in range(4):
         dU = _cplx(rng, U.shape)
