@@ -63,7 +63,9 @@ def dsbcg(apply_A, B, sigma, tol, dtol=1e-12, max_vectors=None, freeze=True,
               below).  Meaningful with freeze=False: a frozen system's
               iterate is no longer the Galerkin iterate.
 
-    Returns (X, info) with X of shape (s, m, n).
+    Returns (X, info) with X of shape (s, m, n).  info["frozen_at"][j, i] is
+    the number of Lanczos vectors after which system (i, j) met tol and was
+    frozen (-1: never frozen).
     """
     B = np.asarray(B, dtype=np.complex128)
     if B.ndim == 1:
@@ -93,6 +95,7 @@ def dsbcg(apply_A, B, sigma, tol, dtol=1e-12, max_vectors=None, freeze=True,
     X = np.zeros((s, m, n), dtype=np.complex128)
     active = np.ones((s, m), dtype=bool)
     relres = np.full((s, m), np.inf)
+    frozen_at = np.full((s, m), -1)      # vector count at which (j, i) was frozen
     deflations = 0
     deflated_at = []
 
@@ -114,7 +117,10 @@ def dsbcg(apply_A, B, sigma, tol, dtol=1e-12, max_vectors=None, freeze=True,
             rr = np.linalg.norm(R, axis=1) / np.where(bnorm[cols] > 0, bnorm[cols], 1.0)
             relres[j, cols] = rr
             if freeze:
-                active[j, cols[rr <= tol]] = False
+                done = cols[rr <= tol]
+                active[j, done] = False
+                first = done[frozen_at[j, done] < 0]
+                frozen_at[j, first] = len(V)
 
     converged = False
     while pending and len(V) < max_vectors:
@@ -200,7 +206,8 @@ def dsbcg(apply_A, B, sigma, tol, dtol=1e-12, max_vectors=None, freeze=True,
         converged = bool(np.all(relres <= tol))
         active[:] = was_active
     info = dict(nvec=len(V), deflations=deflations, deflated_at=deflated_at,
-                relres=relres, converged=converged, invariant=not pending)
+                relres=relres, converged=converged, invariant=not pending,
+                frozen_at=frozen_at)
     if est is not None:
         info["est_relres"] = est
     if keep_basis:

@@ -322,3 +322,40 @@ def test_rational_inverse_square_root(small):
     for i in range(B.shape[0]):
         err = np.linalg.norm(Y[i] - Yd[i])
         assert err <= bound * np.linalg.norm(B[i]) + 1e-9 * np.linalg.norm(Yd[i]), i
+
+
+def test_frozen_systems_are_not_updated(small):
+    """Freezing (Sec. 4): once (i, j) meets tol it is no longer updated, so its
+    final iterate is the iterate after the vector count at which it froze."""
+    dims, Ad, B, sigma, Aop = small
+    m = B.shape[0]
+    tol = 1e-8
+    X, info = dsbcg(Aop, B, sigma, tol=tol, check_every=m)
+    assert info["converged"]
+    fa = info["frozen_at"]
+    assert np.all(fa > 0)
+    assert len(np.unique(fa)) > 1                      # systems freeze at different times
+    assert fa[-1].max() <= fa[0].min()                 # the largest shift converges first
+    for k in np.unique(fa):
+        Xk, _ = dsbcg(Aop, B, sigma, tol=0.0, freeze=False, stop_after_vectors=int(k))
+        for j, i in zip(*np.nonzero(fa == k)):
+            assert np.array_equal(X[j, i], Xk[j, i]), (j, i, k)
+    rr = true_relres(Aop, B, sigma, X)
+    assert rr.max() <= tol
+
+
+def test_frozen_at_survives_a_capped_solve(small):
+    """With a vector cap the smallest shift does not converge; the final
+    residual pass must keep the freeze points of the systems frozen earlier."""
+    dims, Ad, B, sigma, Aop = small
+    m = B.shape[0]
+    tol = 1e-8
+    _, full = dsbcg(Aop, B, sigma, tol=tol, check_every=m)
+    cap = int(full["frozen_at"][0].min()) - m       # before the smallest shift meets tol
+    X, info = dsbcg(Aop, B, sigma, tol=tol, check_every=m, max_vectors=cap)
+    assert not info["converged"] and info["nvec"] == cap
+    fa = info["frozen_at"]
+    early = fa[-1] > 0
+    assert early.all() and fa[-1].max() < cap        # the largest shift froze before the cap
+    assert np.array_equal(fa[-1], full["frozen_at"][-1])
+    assert np.all(fa[0] < 0)
