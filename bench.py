@@ -39,6 +39,19 @@ UNIT = "systems/s"
 KCLASS = ["dslash", "gram", "update", "shift", "small", "residual", "other"]
 
 
+# Conventional Wilson-Dirac flop count per site and field for one D
+# application: 1320 for the eight hops (spin projection, SU(3) multiply,
+# reconstruction, accumulation) plus 48 for the diagonal term.
+WILSON_FLOP_PER_SITE = 1368
+
+
+def fp64_alu_peak_tflops(sm_mhz):
+    """FP64 FMA peak of a GB300 from unit counts and the SM clock: 152 SMs,
+    each with 4 sub-partitions that retire one warp-wide (32-lane) FP64
+    instruction every 64 cycles, i.e. 2 FP64 FMA (4 flop) per SM per clock."""
+    return 152 * 2 * 2 * float(sm_mhz) * 1e6 / 1e12
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -372,6 +385,32 @@ def run_ours(args):
                               "block_steps": st64["block_steps"], "restarts": st64["restarts"],
                               "max_true_relres": float(st64["true_relres"].max()),
                               "mixed_over_fp64": round(value / world / (m * s / t64), 2)}
+        # the FP64 stencil is bound by the FP64 pipe, not by HBM: time its D
+        # launches (library CUDA events) on the workload's m fields
+        try:
+            ctx.set_profiling(True)
+            ctx.apply("A", B, storage="fp64")
+            ctx.read_profile()
+            reps = 3
+            for _ in range(reps):
+                ctx.apply("A", B, storage="fp64")
+            kms64, kl64 = ctx.read_profile()
+            ms_launch = kms64["dslash"] / kl64["dslash"]
+            V = n // 12
+            flop = WILSON_FLOP_PER_SITE * V * m
+            sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+            peak64 = fp64_alu_peak_tflops(sm_mhz)
+            ach = flop / (ms_launch / 1e3) / 1e12
+            gb = (2.0 * m * n * 16 + 36.0 * V * 16) / 1e9
+            line["fp64_plain"]["stencil_roofline"] = {
+                "kernel": "dslash (FP64)", "bound": "alu", "achieved": round(ach, 4), "peak": round(peak64, 4),
+                "unit": "TFLOP/s", "frac": round(ach / peak64, 4), "ms_per_launch": round(ms_launch, 4),
+                "flop_per_launch": flop, "hbm_GBps": round(gb / (ms_launch / 1e3), 1),
+                "peak_source": f"derived: 152 SMs x 2 FP64 FMA/clock x 2 flop x {sm_mhz:.0f} MHz"}
+        except Exception as e:           # the FP64 stencil figure must not cost the bench line
+            line["fp64_plain"]["stencil_roofline"] = {"error": repr(e)[:300]}
+        finally:
+            ctx.set_profiling(False)
     if rank == 0 and world == 1 and not args.no_cpu:
         total_vec = fp64_mvms if fp64_mvms else stats[-1]["mvms"]
         v, cores, wall, per_vec = oracle_sample(wl, args.cpu_vectors, total_vec)

@@ -38,3 +38,12 @@ def test_reference_line_contract():
 
 def test_reference_other_ranks_are_silent():
     assert _run({"RANK": "1", "WORLD_SIZE": "2"}) == []
+
+
+def test_fp64_alu_peak_from_unit_counts():
+    """The derived FP64 peak at the GB300's maximum SM clock (2070 MHz) is the
+    nominal FP64 rate of about 1.25 TFLOP/s."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert abs(bench.fp64_alu_peak_tflops(2070) - 1.25) < 0.02
+    assert bench.WILSON_FLOP_PER_SITE == 1320 + 48
