@@ -108,3 +108,25 @@ def test_binding_matches_header_layout(tmp_path):
         assert got[("status", nm)] == code
     for q, nm in enumerate(dsbcg.KCLASS[:7]):
         assert got[("kclass", nm)] == q
+
+
+def test_product_never_reaches_the_oracle():
+    """The library, its binding and the input generators import, include or
+    name no module of oracle/ (the oracle is test infrastructure), and the
+    oracle imports nothing of the product package (its inputs are passed in)."""
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pkg = os.path.join(root, "paper_1205_0359_gb300")
+    pat = re.compile(r"^\s*(from\s+oracle\b|import\s+oracle\b)|#\s*include\s*[<\"][^>\"]*oracle", re.M)
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                with open(os.path.join(dirpath, f)) as fh:
+                    assert not pat.search(fh.read()), f
+    with open(os.path.join(root, "include", "dsbcg.h")) as fh:
+        assert "oracle" not in fh.read()
+    opat = re.compile(r"^\s*(from|import)\s+paper_1205_0359_gb300\b", re.M)
+    for f in os.listdir(os.path.join(root, "oracle")):
+        if f.endswith(".py"):
+            with open(os.path.join(root, "oracle", f)) as fh:
+                assert not opat.search(fh.read()), f
