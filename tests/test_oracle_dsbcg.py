@@ -359,3 +359,26 @@ def test_frozen_at_survives_a_capped_solve(small):
     assert early.all() and fa[-1].max() < cap        # the largest shift froze before the cap
     assert np.array_equal(fa[-1], full["frozen_at"][-1])
     assert np.all(fa[0] < 0)
+
+
+def test_zero_right_hand_side_is_deflated(small):
+    """b_2 = 0: the zero candidate is dropped when it comes up, right after
+    v_1 is built from b_1 (Sec. 3 deflation); x_2j = 0 exactly, and the other
+    systems are solved as without it."""
+    dims, Ad, B, sigma, Aop = small
+    Bz = B.copy()
+    Bz[1] = 0.0
+    X, info = dsbcg(Aop, Bz, sigma, tol=1e-12)
+    assert info["converged"] and info["deflations"] >= 1 and info["deflated_at"][0] == 1
+    assert np.all(X[:, 1] == 0)
+    Xd = dense_solve(Ad, Bz[[0, 2]], sigma)
+    err = np.linalg.norm(X[:, [0, 2]] - Xd, axis=2) / np.linalg.norm(Xd, axis=2)
+    assert err.max() < 1e-10
+
+
+def test_all_zero_B(small):
+    """B = 0: no Lanczos vector is built and X = 0 is the exact solution."""
+    dims, Ad, B, sigma, Aop = small
+    X, info = dsbcg(Aop, np.zeros_like(B), sigma, tol=1e-12)
+    assert info["nvec"] == 0 and info["converged"] and info["deflations"] == B.shape[0]
+    assert np.all(X == 0)
