@@ -5,9 +5,11 @@ A step is one complete solve (sigma_j I + D^H D) X_j = B, j = 1..12, for
 12 right-hand sides on a 16^3 x 32 lattice (Wilson, kappa = 0.125, smooth
 random SU(3) links), to a true FP64 relative residual <= 1e-8 for every
 (rhs, shift): FP32 storage of fields and links, FP32 arithmetic on them,
-FP64 block coefficients, deflation, shift recurrences and true-residual
-restarts.  Inputs are resident in HBM when the timed region starts and the
-working set of one block step (~9 GB) is far larger than L2.
+IEEE FP64 block coefficients, deflation, shift recurrences, true residuals
+and restarts (reliable updates).  Inputs are resident in HBM when the timed
+region starts and the working set of one block step (~9 GB) is far larger
+than L2.  The double-float form of the reliable updates (an opt-in of the
+library) is timed beside it over the same number of steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -61,12 +63,12 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def workload_config(wl, storage):
+def workload_config(wl, storage, reliable="FP64"):
     return {
         "workload": (f"{WORKLOAD}: Wilson D^H D on {'x'.join(map(str, wl['dims']))}, kappa {wl['kappa']}, "
                      f"m={wl['B'].shape[0]} Z2 RHS, s={len(wl['sigma'])} shifts "
                      f"{wl['sigma'][0]:.0e}..{wl['sigma'][-1]:.0e}, true residual <= {wl['tol']:.0e}, "
-                     f"{storage} storage + {'FP64' if storage == 'fp64' else 'double-float'} reliable updates"),
+                     f"{storage} storage + {reliable} reliable updates and m x m work"),
         "lattice": list(wl["dims"]), "m": int(wl["B"].shape[0]), "s": int(len(wl["sigma"])),
         "tol": wl["tol"], "storage": storage,
         "l2": "no flush: one block step streams ~9 GB, far above the 129 MB L2",
@@ -217,7 +219,7 @@ def run_ours(args):
     B = torch.from_numpy(wl["B"]).to(dev)
     X = torch.empty((s, m, n), dtype=torch.complex128, device=dev)
 
-    def solve(storage=args.storage, Bx=B, Xx=X, fp64res=False):
+    def solve(storage=args.storage, Bx=B, Xx=X, fp64res=True):
         _, st = ctx.solve(Bx, wl["sigma"], wl["tol"], storage=storage, out=Xx, fp64_residuals=fp64res)
         return st
 
@@ -241,6 +243,7 @@ def run_ours(args):
     value = replica_value(world, m, s, args.steps, ms_total / 1e3)
     maxrel = max(float(st["true_relres"].max()) for st in stats)
     ok = all(st["code"] == 0 for st in stats) and maxrel <= wl["tol"]
+    Xmix = X.clone()                       # the headline solution, for the FP64 comparison
 
     # per-kernel breakdown: one more solve with the library's per-launch CUDA
     # events on (restarts then run one at a time, so that each class's event
@@ -261,8 +264,11 @@ def run_ours(args):
             kernels[q] = {"ms_per_step": kms[q] / prof_steps, "launches_per_step": kla[q] / prof_steps,
                           "GB_per_step": kby[q] / prof_steps / 1e9, "GBps": gbs,
                           "frac_of_hbm": gbs / peak}
-    memory_bound = [q for q in ("dslash", "gram", "update", "shift", "residual") if q in kernels]
-    dom = max(memory_bound, key=lambda q: kms[q])
+    # HBM-bound classes in the reduced-precision storage; the true-residual
+    # class runs the FP64 stencil, which is bound by the FP64 pipe
+    hbm_bound = [q for q in ("dslash", "gram", "update", "shift") if q in kernels]
+    dom = max(hbm_bound, key=lambda q: kms[q])
+    clk_mhz = (clk or {}).get("sm_mhz") or 2070.0
 
     def roof(q):
         achieved = kby[q] / (kms[q] / 1e3) / 1e9
@@ -275,6 +281,24 @@ def run_ours(args):
                 "algorithmic_GB_per_launch": round(kby[q] / kla[q] / 1e9, 4) if kla[q] else None,
                 "peak_source": f"{peak_kind} HBM copy bandwidth"}
 
+    def residual_roof():
+        """FP64 true residuals r = b - sigma x - A x: each call applies D and
+        D^H to its fields (FP64 stencil, 1368 flop per site and field each)
+        plus a streaming residual kernel; the class's flops over its event
+        time against the FP64 ALU peak at the sampled SM clock."""
+        calls = kla["residual"] / 4.0                 # 2 stencils + residual + column reduction
+        V = wl["B"].shape[1] // 12
+        nfields = (kby["residual"] / 16.0 - 72.0 * V * calls) / (8.0 * wl["B"].shape[1])
+        flop = 2.0 * WILSON_FLOP_PER_SITE * V * nfields
+        ach = flop / (kms["residual"] / 1e3) / 1e12
+        pk = fp64_alu_peak_tflops(clk_mhz)
+        return {"kernel": "residual (FP64 stencil D, D^H + r = b - sigma x - A x)", "bound": "alu",
+                "achieved": round(ach, 4), "peak": round(pk, 4), "unit": "TFLOP/s", "frac": round(ach / pk, 4),
+                "traffic": None, "flop_per_solve": flop, "fields_per_solve": round(nfields, 1),
+                "ms_per_solve": round(kms["residual"], 3),
+                "peak_source": f"derived: 152 SMs x 2 FP64 FMA/clock x 2 flop x {clk_mhz:.0f} MHz (sampled)"}
+
+    top = max(hbm_bound + (["residual"] if "residual" in kernels else []), key=lambda q: kms[q])
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
@@ -284,13 +308,16 @@ def run_ours(args):
         "valid": ok, "max_true_relres": maxrel,
         "solver": {"block_steps": stats[-1]["block_steps"], "restarts": stats[-1]["restarts"],
                    "mvms": stats[-1]["mvms"], "deflations": stats[-1]["deflations"]},
-        "roofline": roof(dom),
+        "roofline": residual_roof() if top == "residual" else roof(dom),
+        "hbm_roofline": roof(dom),
         "stencil_roofline": roof("dslash"),
         "kernels": kernels,
         "kernels_from": "one extra solve with per-launch CUDA events (restarts serialised)",
         # launches per solve are the same with and without the events
         "gpu_launches": int(round(sum(kla.values()) / prof_steps * args.steps)),
     }
+    if "residual" in kernels:
+        line["residual_roofline"] = residual_roof()
     if clk is not None:
         line["clocks"] = clk
     ctx.set_profiling(False)
@@ -309,23 +336,25 @@ def run_ours(args):
     line["e2e"] = {"value": round(replica_value(world, m, s, 1, e2e_s), 3), "unit": UNIT,
                    "h2d_bytes_per_step": int(Bh.numel() * 16), "d2h_bytes_per_step": int(Xh.numel() * 16)}
 
-    # the same mixed solve with IEEE FP64 reliable updates and m x m work
-    # (dsbcg_params.fp64_residuals) instead of double-float
-    if rank == 0 and not args.no_fp64:
-        solve(fp64res=True)
+    # the same mixed solve with the library's opt-in double-float reliable
+    # updates and m x m work (dsbcg_params.fp64_residuals = 0), timed over
+    # the same number of steps as the headline
+    if rank == 0 and not args.no_df32:
+        for _ in range(args.warmup):
+            solve(fp64res=False)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        nfr = 2
-        stf = [solve(fp64res=True) for _ in range(nfr)]
+        stf = [solve(fp64res=False) for _ in range(args.steps)]
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        tf = e0.elapsed_time(e1) / 1e3 / nfr
-        line["fp64_reliable_updates"] = {
-            "value": round(m * s / tf, 3), "unit": UNIT, "ms_per_step": round(tf * 1e3, 1), "steps": nfr,
+        tf = e0.elapsed_time(e1) / 1e3 / args.steps
+        line["double_float_reliable_updates"] = {
+            "value": round(m * s / tf, 3), "unit": UNIT, "ms_per_step": round(tf * 1e3, 1), "steps": args.steps,
             "block_steps": stf[-1]["block_steps"], "restarts": stf[-1]["restarts"],
             "max_true_relres": float(max(st["true_relres"].max() for st in stf)),
-            "note": "FP32 storage; true residuals, solution accumulation and m x m work in IEEE FP64"}
+            "note": ("FP32 storage; true residuals, solution accumulation and m x m work in double-float "
+                     "(48-bit significands on the FP32 pipes), the library's opt-in")}
 
     # gauge-link force of the gradient workload (16^3 x 32, m = s = 8, FP32):
     # dsbcg_force on device X and adjoint Lambda, whole call and force kernel
@@ -366,25 +395,44 @@ def run_ours(args):
         fctx.close()
         del Xf, Lf, dU
 
+    def leg(key, fn):
+        """An optional leg: its error is recorded in the line, never raised."""
+        try:
+            line[key] = fn()
+        except Exception as e:                   # noqa: BLE001 - a failed leg must not cost the line
+            line[key] = {"error": repr(e)[:400]}
+        torch.cuda.synchronize(dev)
+        torch.cuda.empty_cache()
+
     if rank == 0 and not args.no_compare:
-        line["comparison"] = run_comparison(dev, stream)
+        leg("comparison", lambda: run_comparison(dev, stream))
+    clk_mhz = (clk or {}).get("sm_mhz") or 2070.0
+    if rank == 0 and not args.no_w3:
+        leg("w3_precision_ladder", lambda: run_w3_ladder(dev, stream, peak, clk_mhz))
     if rank == 0 and args.sweeps:
         line["sweeps"] = run_sweeps(dev, stream)
 
     fp64_mvms = None
     if rank == 0 and not args.no_fp64:
+        X64 = torch.empty_like(X)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        st64 = solve(storage="fp64")
+        st64 = solve(storage="fp64", Xx=X64)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         t64 = e0.elapsed_time(e1) / 1e3
         fp64_mvms = st64["mvms"]
+        # per-(rhs, shift) error of the headline (mixed) solution against the
+        # plain FP64 solution; both meet tol in their own FP64 true residual
+        err = (torch.linalg.vector_norm(Xmix - X64, dim=-1) / torch.linalg.vector_norm(X64, dim=-1)).cpu().numpy()
         line["fp64_plain"] = {"value": round(m * s / t64, 4), "unit": UNIT, "ms_per_step": round(t64 * 1e3, 1),
                               "block_steps": st64["block_steps"], "restarts": st64["restarts"],
                               "max_true_relres": float(st64["true_relres"].max()),
-                              "mixed_over_fp64": round(value / world / (m * s / t64), 2)}
+                              "mixed_over_fp64": round(value / world / (m * s / t64), 2),
+                              "mixed_error_vs_fp64": {"max": float(err.max()),
+                                                      "per_pair": [[float(f"{v:.3e}") for v in r] for r in err]}}
+        del X64
         # the FP64 stencil is bound by the FP64 pipe, not by HBM: time its D
         # launches (library CUDA events) on the workload's m fields
         try:
@@ -415,11 +463,16 @@ def run_ours(args):
         total_vec = fp64_mvms if fp64_mvms else stats[-1]["mvms"]
         v, cores, wall, per_vec = oracle_sample(wl, args.cpu_vectors, total_vec)
         line["cpu_baseline"] = {
-            "value": round(v, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "value": round(v, 6), "unit": UNIT, "cores": cores, "host_cores": os.cpu_count(), "kind": "oracle",
             "sample": (f"numpy FP64 oracle, first {args.cpu_vectors} band-Lanczos vectors of the same "
                        f"workload ({wall:.1f} s, {per_vec:.2f} s/vector), scaled to the "
                        f"{total_vec} single-vector A applications of the FP64 GPU solve")}
     ctx.close()
+    del X, Xmix, B
+    torch.cuda.empty_cache()
+    # the 32^3 x 64 workload needs most of the device: run it alone
+    if rank == 0 and args.w5:
+        leg("w5_full_size", lambda: run_w5(dev, stream, peak, clk_mhz, fp64=not args.no_fp64))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -473,6 +526,119 @@ def run_comparison(dev, stream, name="cmp_16x16x16x16", storage="fp64", dims=Non
                         f"m={m} Gaussian RHS, "
                         f"s={s} shifts {sig[0]:.0e}..{sig[-1]:.0e}, tol {wl['tol']:.0e}, {storage} storage",
             "algorithms": out}
+
+
+def _timed_solve(ctx, B, sig, tol, storage, X, dev, stream):
+    """One solve timed with CUDA events on the stream, after a one-step
+    warm-up solve of the same shape (workspace and restart lanes allocated,
+    links packed for the precision)."""
+    import torch
+    ctx.solve(B, sig, tol, storage=storage, out=X, max_block_steps=1, raise_on_error=False)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    _, st = ctx.solve(B, sig, tol, storage=storage, out=X)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    return st, e0.elapsed_time(e1)
+
+
+def _stencil_rate(ctx, B, storage, m, n, peak, clk_mhz):
+    """D on the m fields of B in `storage` (dsbcg_apply), the stencil launch
+    timed by the library's CUDA events: GB/s of its algorithmic bytes (fields
+    in and out, links once) against the HBM peak, and TFLOP/s (1368 flop per
+    site and field)."""
+    eb = {"fp64": 16, "fp32": 8, "bf16": 4, "fp16": 4}[storage]
+    V = n // 12
+    ctx.set_profiling(True)
+    ctx.apply("D", B, storage=storage)
+    ctx.read_profile()
+    reps = 5
+    for _ in range(reps):
+        ctx.apply("D", B, storage=storage)
+    kms, kl = ctx.read_profile()
+    ctx.set_profiling(False)
+    ms = kms["dslash"] / kl["dslash"]
+    gb = (2.0 * m * n * eb + 36.0 * V * eb) / 1e9
+    out = {"ms_per_launch": round(ms, 4), "GBps": round(gb / (ms / 1e3), 1),
+           "frac_of_hbm": round(gb / (ms / 1e3) / peak, 4),
+           "TFLOPs": round(WILSON_FLOP_PER_SITE * V * m / (ms / 1e3) / 1e12, 3)}
+    if storage == "fp64":
+        pk = fp64_alu_peak_tflops(clk_mhz)
+        out["bound"] = "alu"
+        out["frac_of_fp64_peak"] = round(out["TFLOPs"] / pk, 4)
+    else:
+        out["bound"] = "hbm"
+    return out
+
+
+def run_w3_ladder(dev, stream, peak, clk_mhz):
+    """The storage-precision ladder on 24^3 x 48 (m = s = 8, shifts 1e-4..1,
+    tol 1e-8): per storage (FP64, FP32, BF16, FP16; the last three inside
+    FP64 reliable updates) systems/s, the stencil's GB/s and roofline
+    fraction, and the per-(rhs, shift) error against the FP64-storage
+    solution."""
+    import torch
+    from paper_1205_0359_gb300 import dsbcg, synth
+    wl = synth.make_workload("w3_24x24x24x48")
+    m, s, n = wl["B"].shape[0], len(wl["sigma"]), wl["B"].shape[1]
+    ctx = dsbcg.Context(wl["dims"], torch.from_numpy(wl["U"]).to(dev), wl["kappa"], stream=stream)
+    B = torch.from_numpy(wl["B"]).to(dev)
+    X64 = torch.empty((s, m, n), dtype=torch.complex128, device=dev)
+    X = torch.empty_like(X64)
+    out = {"workload": (f"w3_24x24x24x48: Wilson D^H D, kappa {wl['kappa']}, m={m} Gaussian RHS, s={s} shifts "
+                        f"{wl['sigma'][0]:.0e}..{wl['sigma'][-1]:.0e}, tol {wl['tol']:.0e}"), "storages": {}}
+    n64 = None
+    for storage in ("fp64", "fp32", "bf16", "fp16"):
+        dst = X64 if storage == "fp64" else X
+        st, ms = _timed_solve(ctx, B, wl["sigma"], wl["tol"], storage, dst, dev, stream)
+        row = {"systems_per_s": round(m * s / (ms / 1e3), 3), "ms_per_solve": round(ms, 1),
+               "block_steps": st["block_steps"], "restarts": st["restarts"],
+               "max_true_relres": float(st["true_relres"].max()), "valid": st["code"] == 0,
+               "stencil": _stencil_rate(ctx, B, storage, m, n, peak, clk_mhz)}
+        if storage == "fp64":
+            n64 = torch.linalg.vector_norm(X64, dim=-1)
+        else:
+            err = (torch.linalg.vector_norm(X - X64, dim=-1) / n64).cpu().numpy()
+            row["error_vs_fp64_storage"] = {"max": float(err.max()),
+                                            "per_pair": [[float(f"{v:.3e}") for v in r] for r in err]}
+        out["storages"][storage] = row
+    ctx.close()
+    del X, X64, B
+    return out
+
+
+def run_w5(dev, stream, peak, clk_mhz, fp64=True):
+    """32^3 x 64, m = 16 (b_16 = b_1 + 1e-9 noise), s = 8 shifts 1e-5..1,
+    tol 1e-8 (~140 GB of HBM in FP32 storage): mixed precision (FP32 storage,
+    FP64 reliable updates) against the plain FP64 form, one timed solve each,
+    and the FP32 stencil's roofline fraction."""
+    import torch
+    from paper_1205_0359_gb300 import dsbcg, synth
+    wl = synth.make_workload("w5_32x32x32x64")
+    m, s, n = wl["B"].shape[0], len(wl["sigma"]), wl["B"].shape[1]
+    out = {"workload": (f"w5_32x32x32x64: Wilson D^H D, kappa {wl['kappa']}, m={m} Gaussian RHS with "
+                        f"b_16 = b_1 + 1e-9 noise, s={s} shifts {wl['sigma'][0]:.0e}..{wl['sigma'][-1]:.0e}, "
+                        f"tol {wl['tol']:.0e}")}
+    B = torch.from_numpy(wl["B"]).to(dev)
+    X = torch.empty((s, m, n), dtype=torch.complex128, device=dev)
+    for storage in (("fp32", "fp64") if fp64 else ("fp32",)):
+        ctx = dsbcg.Context(wl["dims"], torch.from_numpy(wl["U"]).to(dev), wl["kappa"], stream=stream)
+        # the stencil first: dsbcg_apply's temporaries would not fit beside
+        # the solver's workspace
+        stencil = _stencil_rate(ctx, B, storage, m, n, peak, clk_mhz)
+        torch.cuda.empty_cache()
+        st, ms = _timed_solve(ctx, B, wl["sigma"], wl["tol"], storage, X, dev, stream)
+        out[storage] = {"systems_per_s": round(m * s / (ms / 1e3), 4), "ms_per_solve": round(ms, 1),
+                        "block_steps": st["block_steps"], "restarts": st["restarts"],
+                        "deflations": st["deflations"], "max_true_relres": float(st["true_relres"].max()),
+                        "valid": st["code"] == 0, "stencil": stencil}
+        ctx.close()
+        torch.cuda.empty_cache()
+    if fp64:
+        out["mixed_over_fp64"] = round(out["fp32"]["systems_per_s"] / out["fp64"]["systems_per_s"], 2)
+    del X, B
+    return out
 
 
 def run_sweeps(dev, stream, storage="fp64"):
@@ -554,8 +720,9 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * float(np.mean(walls)), 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": workload_config(wl, "fp64"),
-        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+        "data": "synthetic", "config": workload_config(wl, "fp32"),
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores, "host_cores": os.cpu_count(),
+                         "kind": "oracle",
                          "sample": (f"each step: numpy FP64 oracle for {args.ref_vectors} band-Lanczos vectors, "
                                     f"scaled to a {total_vec}-vector solve")},
         "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -571,13 +738,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16", "fp64"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
+    ap.add_argument("--no-df32", action="store_true", help="skip the double-float reliable-update form")
+    ap.add_argument("--no-w3", action="store_true", help="skip the 24^3 x 48 storage-precision ladder")
+    ap.add_argument("--w5", action="store_true", help="also run the 32^3 x 64 workload (mixed and plain FP64)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-force", action="store_true", help="skip the gauge-force timing")
     ap.add_argument("--sweeps", action="store_true",
                     help="also run the paper's shift and right-hand-side sweeps (DSBlockCG vs shifted CG)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the paper's algorithm comparison (CG, block CG, shifted CG, DSBlockCG)")
-    ap.add_argument("--cpu-vectors", type=int, default=2)
+    ap.add_argument("--cpu-vectors", type=int, default=4)
     ap.add_argument("--ref-vectors", type=int, default=1)
     # single-vector A applications of a whole FP64 solve of the workload (the
     # plain FP64 GPU form measured 1488 on 16^3 x 32, m = s = 12); the main

@@ -54,8 +54,9 @@ typedef enum {
 /* Storage precision of spinor fields and links inside the Krylov iteration.
  * Arithmetic on FP32/BF16/FP16 storage is FP32.  The m x m block
  * coefficients, deflation, per-shift recurrences, true residuals and
- * accumulated solutions are FP64 for FP64 storage; for the reduced storages
- * they are double-float by default and FP64 with dsbcg_params.fp64_residuals.
+ * accumulated solutions are IEEE FP64 by default (dsbcg_params.fp64_residuals
+ * = 1); for the reduced storages dsbcg_params.fp64_residuals = 0 selects
+ * double-float arithmetic for them instead.
  * DSBCG_PREC_DF32 ("double-float"): each real number is an unevaluated sum
  * hi + lo of two FP32 words (48-bit significand, FP32 exponent range,
  * arithmetic on the FP32 pipes through error-free transformations).  It is
@@ -69,6 +70,10 @@ typedef enum {
     DSBCG_PREC_FP16 = 3,
     DSBCG_PREC_DF32 = 4
 } dsbcg_prec;
+
+/* The operator a context solves with (dsbcg_set_operator). */
+#define DSBCG_OPERATOR_NORMAL 0     /* A = D^H D on full-lattice fields, n = 12 V (default) */
+#define DSBCG_OPERATOR_SCHUR 1      /* Ahat = Dhat^H Dhat on odd-site fields, n = 6 V */
 
 /* Operators for dsbcg_apply. */
 typedef enum {
@@ -89,10 +94,12 @@ typedef struct {
     int freeze_converged;   /* stop updating converged (i, j) systems (Sec. 4) */
     int refine;             /* 1: after the joint solve, restart each unconverged shift
                                separately (block CG) until its true residual meets tol */
-    int fp64_residuals;     /* reduced storages only.  0 (default): true residuals,
+    int fp64_residuals;     /* reduced storages only.  1 (default): true residuals,
                                accumulated solutions and the m x m coefficient work in
-                               double-float arithmetic (DSBCG_PREC_DF32) on the FP32
-                               pipes; 1: all of them in IEEE FP64, as with FP64 storage */
+                               IEEE FP64, as with FP64 storage; 0 (opt-in): all of them
+                               in double-float arithmetic (DSBCG_PREC_DF32) on the FP32
+                               pipes, about 1.2x faster on GB300, where FP64 runs at
+                               1/64 of the FP32 rate */
     int x0;                 /* 1: X's input is an initial guess X_0 for every system (a
                                resumed solve): the joint block solve is skipped and
                                each shift is restarted from its own true residual
@@ -128,7 +135,8 @@ typedef struct {
 #define DSBCG_KCLASS_RESIDUAL 5     /* true residuals (FP64 or double-float) */
 #define DSBCG_KCLASS_OTHER 6
 
-/* Fill *p with the defaults (FP32 storage, automatic dtol, freezing on). */
+/* Fill *p with the defaults (FP32 storage, FP64 reliable updates and m x m
+ * work, automatic dtol, freezing on). */
 void dsbcg_params_default(dsbcg_params* p);
 
 /* Create a context for one lattice and gauge field.
@@ -153,12 +161,11 @@ dsbcg_status dsbcg_update_gauge(dsbcg_ctx* ctx, const void* gauge);
  * factorisation of sigma_j I + T per shift; directions that become linearly
  * dependent are deflated (Sec. 1, Sec. 3).  With FP32/BF16/FP16 storage the
  * Krylov iteration runs in reduced precision inside a loop that recomputes
- * true residuals in double-float arithmetic (DSBCG_PREC_DF32; FP64 with
- * params->fp64_residuals) and restarts (reliable updates); with FP64
- * storage residuals are FP64.  A double-float
- * residual carries an absolute error of roughly 2^-44 |A| |x|, so it
- * certifies tol down to about 1e-13 times the condition number of
- * sigma_j I + A.
+ * true residuals in FP64 (double-float arithmetic, DSBCG_PREC_DF32, with
+ * params->fp64_residuals = 0) and restarts (reliable updates); with FP64
+ * storage residuals are FP64.  A double-float residual carries an absolute
+ * error of roughly 2^-44 |A| |x|, so it certifies tol down to about 1e-13
+ * times the condition number of sigma_j I + A.
  *   m:     number of right-hand sides, 1 <= m <= 32
  *   B:     device or host complex128 [m][n]
  *   s:     number of shifts, 1 <= s <= 64
@@ -172,6 +179,89 @@ dsbcg_status dsbcg_update_gauge(dsbcg_ctx* ctx, const void* gauge);
  * DSBCG_NOT_CONVERGED (X still written) when a cap is hit. */
 dsbcg_status dsbcg_solve(dsbcg_ctx* ctx, int m, const void* B, int s, const double* sigma,
                          double tol, const dsbcg_params* params, void* X, dsbcg_stats* stats);
+
+/* Solve the shifted systems as dsbcg_solve does and write their rational
+ * combination
+ *     Y = alpha0 B + sum_j alpha_j X_j   (= r(A) B for the partial fraction
+ *                                          r(x) = alpha0 + sum_j alpha_j / (x + sigma_j)),
+ * the use of the shifted solves named in Sec. 1 (rational approximations in
+ * RHMC).  Y is formed on the device in one pass over the final solutions,
+ * shifts summed in index order, in FP64 arithmetic.  Every (i, j) system meets
+ * tol as in dsbcg_solve, so ||y_i - r(A) b_i|| <= tol ||b_i|| sum_j |alpha_j| /
+ * lambda_min(sigma_j I + A).
+ *   alpha0: real; alpha: HOST double[s], finite
+ *   Y:      device or host complex128 [m][n], output
+ *   X:      NULL (the per-shift solutions are not written: the caller's
+ *           output is s times smaller) or device or host [s][m][n]
+ * Other arguments, results and status codes as dsbcg_solve; params->x0 needs X. */
+dsbcg_status dsbcg_solve_rational(dsbcg_ctx* ctx, int m, const void* B, int s, const double* sigma,
+                                  double alpha0, const double* alpha, double tol, const dsbcg_params* params,
+                                  void* Y, void* X, dsbcg_stats* stats);
+
+/* Backward pass of dsbcg_solve: gradients of a real loss L through
+ * X_j = (sigma_j I + A)^{-1} B, given the incoming gradients G_j = dL/dX_j.
+ * Not in the paper (its motivation is the RHMC force, Sec. 1).  With
+ * sigma_j I + A hermitian, the adjoint solutions are Lambda_j =
+ * (sigma_j I + A)^{-1} G_j, and
+ *     dL/dB       = g_direct G + sum_j Lambda_j
+ *     dL/dsigma_j = -Re tr(Lambda_j^H X_j)
+ *     dL/dU       = the force of dsbcg_force on (X_j, Lambda_j) with unit weights
+ * (complex gradients in the dL/dRe + i dL/dIm convention).  Every step runs
+ * in the library's kernels:
+ *   - g_weights != NULL: G is ONE block [m][n] and G_j = g_weights[j] G (the
+ *     gradient of a loss of Y = sum_j g_weights[j] X_j, the RHMC case): one
+ *     joint DSBlockCG solve of G for all shifts, Lambda_j scaled by w_j;
+ *   - g_weights == NULL: G is [s][m][n] (one block per shift): all s shifts
+ *     are solved in this one call, each shift's block CG on its own stream
+ *     (the restart lanes of dsbcg_solve), concurrently;
+ *   - X == NULL: the solutions are recomputed from B by a dsbcg_solve
+ *     (memory instead of storage); otherwise X holds them and B may be NULL.
+ * Each adjoint system meets tol like a forward system.
+ *   B:         device or host complex128 [m][n] (needed only when X == NULL)
+ *   X:         NULL or device or host complex128 [s][m][n]
+ *   G:         device or host complex128 [m][n] or [s][m][n], see above
+ *   g_weights: NULL or HOST double[s]
+ *   g_direct:  0, or (with g_weights) the weight of B's direct term in the
+ *              forward output, e.g. alpha0 for dsbcg_solve_rational's Y
+ *   gB:        NULL or device or host complex128 [m][n], output
+ *   gsigma:    NULL or HOST double[s], output
+ *   gU:        NULL or device or host complex128 [site][4][3][3], output
+ *              (computed in FP64 for FP64 storage, else from FP32 fields)
+ *   Lambda:    NULL or device or host complex128 [s][m][n], output
+ *   params:    as dsbcg_solve (x0 is ignored)
+ *   stats:     block steps, mvms, restarts and deflations summed over the
+ *              solves of the call; true_relres and conv_step (if given) are
+ *              those of the adjoint systems; kernel_* are not written.
+ * Returns DSBCG_NOT_CONVERGED if a solve hit a cap (outputs still written). */
+dsbcg_status dsbcg_backward(dsbcg_ctx* ctx, int m, const void* B, int s, const double* sigma, const void* X,
+                            const void* G, const double* g_weights, double g_direct, double tol,
+                            const dsbcg_params* params, void* gB, double* gsigma, void* gU, void* Lambda,
+                            dsbcg_stats* stats);
+
+/* Select the operator of the context's solves and applications.
+ *   DSBCG_OPERATOR_NORMAL: A = D^H D of the Wilson operator (Sec. 1), the
+ *     paper's setting; fields have n = 12 V complex entries.
+ *   DSBCG_OPERATOR_SCHUR: the even-odd preconditioned (Schur complement)
+ *     operator on the odd sites.  With D = 1 - kappa H (H the hopping term,
+ *     which connects only sites of opposite parity x + y + z + t mod 2 when
+ *     every extent is even),
+ *         Dhat = 1 - kappa^2 H_oe H_eo,   Dhat^H = gamma_5 Dhat gamma_5,
+ *         Ahat = Dhat^H Dhat,
+ *     and sigma_j I + Ahat is hpd for sigma_j > 0, so the method applies to it
+ *     unchanged (Sec. 3).  The paper itself uses no such structure (Sec. 4):
+ *     this is a preconditioned variant.  Fields are then odd-site half
+ *     fields of n = 6 V complex entries: the odd sites in increasing
+ *     canonical site order (half index = site / 2), 12 entries each.  D x = b
+ *     follows from the odd-site system Dhat x_o = b_o + kappa H_oe b_e and
+ *     x_e = b_e + kappa H_eo x_o.
+ * dsbcg_solve, dsbcg_solve_rational, dsbcg_apply (D -> Dhat, D^H -> Dhat^H,
+ * A -> Ahat) and the B / sigma gradients of dsbcg_backward act on the
+ * selected operator; dsbcg_force, the link gradient of dsbcg_backward and
+ * dsbcg_apply_static support the normal operator only (DSBCG_ERR_UNSUPPORTED).
+ * Changing the operator frees the context's solver workspace.  Returns
+ * DSBCG_ERR_ARG for an unknown operator, or SCHUR on a lattice with an odd
+ * extent. */
+dsbcg_status dsbcg_set_operator(dsbcg_ctx* ctx, int op);
 
 /* Apply D, D^H or A to m fields: out_i = op(in_i).  The fields are converted
  * to `storage` precision (any dsbcg_prec, including DSBCG_PREC_DF32), the
@@ -193,7 +283,8 @@ dsbcg_status dsbcg_apply(dsbcg_ctx* ctx, int op, int storage, int m, const void*
  *   - the packed working fields live in one static device array of
  *     DSBCG_STATIC_SCRATCH_BYTES (32 MiB) that every GPU which loads the library
  *     holds until the process exits.  op = A needs 3 * m * (n rounded up to a
- *     multiple of 128) * (16, 8 or 4 bytes for FP64, FP32 or FP16/BF16) bytes,
+ *     multiple of 128) * (16, 8 or 4 bytes for FP64 or DF32, FP32, or
+ *     FP16/BF16) bytes,
  *     D and D^H need 2/3 of that; larger requests return DSBCG_ERR_ARG and do
  *     nothing;
  *   - storage precisions other than FP64 need the context's links for that

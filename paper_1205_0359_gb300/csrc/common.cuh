@@ -119,6 +119,8 @@ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2
 __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
 // i * a
 template <class C> __device__ __forceinline__ C ctimesi(C a) { return mk(-a.y, a.x); }
+// -a (exact; a negation modifier of the consuming instruction in FP32/FP64)
+template <class C> __device__ __forceinline__ C cneg(C a) { return mk(-a.x, -a.y); }
 
 // ------------------------------------------------------------ double-float --
 // An unevaluated sum hi + lo of two FP32 numbers with |lo| <= ulp(hi) / 2:

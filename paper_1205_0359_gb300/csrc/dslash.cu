@@ -329,11 +329,142 @@ __global__ void __launch_bounds__(32, (P == PDD || P == P64) ? 12 : 24) dslash_k
     }
 }
 
+// Half-lattice hopping term for the even-odd (Schur) operator.  With every
+// extent even, the sites of one parity p (x + y + z + t = p mod 2) in
+// increasing canonical order have the half index k = site / 2 (each x-row
+// holds Lx / 2 of them), and the hopping term H of D = 1 - kappa H maps
+// parity 1 - p to parity p:
+//     out_f(k) = alpha s_f(k) + beta G5o (H G5i in_f)(x_k),
+// with in_f on parity 1 - p, s_f and out_f on parity p (all half fields of
+// Vh = V / 2 sites) and G5i, G5o optional gamma_5 factors.  The Schur
+// operator on the odd sites, Dhat = 1 - kappa^2 H_oe H_eo, is two such passes.
+template <int P>
+__global__ void __launch_bounds__(32, (P == PDD || P == P64) ? 12 : 24) dslash_half_kernel(
+    typename Tr<P>::S2* __restrict__ out, const typename Tr<P>::S2* __restrict__ in,
+    const typename Tr<P>::S2* __restrict__ src, size_t ld, const typename Tr<P>::S2* __restrict__ links, Geom g,
+    typename Tr<P>::R alpha, typename Tr<P>::R beta, int parity, int g5in, int g5out, const Ctl* __restrict__ ctl,
+    int nf_static, float hscale, int nfg) {
+    using C = typename Tr<P>::C;
+    using R = typename Tr<P>::R;
+    int nf = nf_static;
+    if (ctl) {
+        if (ctl->done) return;
+        nf = ctl->mk;
+    }
+    const int f = (int)(blockIdx.x % (unsigned)nfg);
+    if (f >= nf) return;
+    const int Vh = g.V / 2;
+    const int k = (int)(blockIdx.x / (unsigned)nfg) * 32 + threadIdx.x;
+    if (k >= Vh) return;
+    R inv = R(1), scl = R(1);
+    if constexpr (P == PBF16 || P == PF16) {
+        inv = R(1) / R(hscale);
+        scl = R(hscale);
+    }
+    const size_t plo = (P == PDD) ? ld / 2 : 0;
+    const size_t loff = (P == PDD) ? 36 * (size_t)g.V : 0;
+    const size_t V = (size_t)g.V;
+    // full-lattice site of half index k
+    const int hx = g.L[0] / 2;
+    const int row = k / hx;
+    Site s;
+    s.c[1] = row % g.L[1];
+    s.c[2] = (row / g.L[1]) % g.L[2];
+    s.c[3] = row / (g.L[1] * g.L[2]);
+    s.c[0] = 2 * (k % hx) + ((parity + s.c[1] + s.c[2] + s.c[3]) & 1);
+    const int x = s.c[0] + g.L[0] * row;
+    const R g5i = g5in ? R(-1) : R(1);
+    const typename Tr<P>::S2* fin = in + (size_t)f * ld;
+    C acc[4][3];
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc[sp][a] = mk(R(0), R(0));
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+#pragma unroll
+        for (int dir = 0; dir < 2; ++dir) {
+            float sgn;
+            const int y = neighbour(g, x, s, mu, dir == 0 ? 1 : -1, &sgn);
+            C p[12];
+            SpinorIO<P>::load(fin, (size_t)Vh, (size_t)(y >> 1), p, inv, plo);
+            const R sg = R(sgn);
+            const R su = sg * g5i;
+            const R sl_ = sg;
+            C h[2][3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                C u0 = cscale(p[0 * 3 + a], su), u1 = cscale(p[1 * 3 + a], su);
+                C l0 = cscale(p[2 * 3 + a], sl_), l1 = cscale(p[3 * 3 + a], sl_);
+                if (dir == 0) {
+                    if (mu == 0) { h[0][a] = csub(u0, ctimesi(l1)); h[1][a] = csub(u1, ctimesi(l0)); }
+                    if (mu == 1) { h[0][a] = csub(u0, l1); h[1][a] = cadd(u1, l0); }
+                    if (mu == 2) { h[0][a] = csub(u0, ctimesi(l0)); h[1][a] = cadd(u1, ctimesi(l1)); }
+                    if (mu == 3) { h[0][a] = csub(u0, l0); h[1][a] = csub(u1, l1); }
+                } else {
+                    if (mu == 0) { h[0][a] = cadd(u0, ctimesi(l1)); h[1][a] = cadd(u1, ctimesi(l0)); }
+                    if (mu == 1) { h[0][a] = cadd(u0, l1); h[1][a] = csub(u1, l0); }
+                    if (mu == 2) { h[0][a] = cadd(u0, ctimesi(l0)); h[1][a] = csub(u1, ctimesi(l1)); }
+                    if (mu == 3) { h[0][a] = cadd(u0, l0); h[1][a] = cadd(u1, l1); }
+                }
+            }
+            C uh[2][3];
+            su3_mul<P>(links + (size_t)mu * 9 * V + (dir == 0 ? x : y), V, loff, h, uh, dir != 0);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                acc[0][a] = cadd(acc[0][a], uh[0][a]);
+                acc[1][a] = cadd(acc[1][a], uh[1][a]);
+                C q0 = uh[0][a], q1 = uh[1][a];
+                if (dir == 0) {
+                    if (mu == 0) { acc[2][a] = cadd(acc[2][a], ctimesi(q1)); acc[3][a] = cadd(acc[3][a], ctimesi(q0)); }
+                    if (mu == 1) { acc[2][a] = cadd(acc[2][a], q1); acc[3][a] = csub(acc[3][a], q0); }
+                    if (mu == 2) { acc[2][a] = cadd(acc[2][a], ctimesi(q0)); acc[3][a] = csub(acc[3][a], ctimesi(q1)); }
+                    if (mu == 3) { acc[2][a] = csub(acc[2][a], q0); acc[3][a] = csub(acc[3][a], q1); }
+                } else {
+                    if (mu == 0) { acc[2][a] = csub(acc[2][a], ctimesi(q1)); acc[3][a] = csub(acc[3][a], ctimesi(q0)); }
+                    if (mu == 1) { acc[2][a] = csub(acc[2][a], q1); acc[3][a] = cadd(acc[3][a], q0); }
+                    if (mu == 2) { acc[2][a] = csub(acc[2][a], ctimesi(q0)); acc[3][a] = cadd(acc[3][a], ctimesi(q1)); }
+                    if (mu == 3) { acc[2][a] = cadd(acc[2][a], q0); acc[3][a] = cadd(acc[3][a], q1); }
+                }
+            }
+        }
+    }
+    C p[12];
+    const bool has_src = src != nullptr;
+    if (has_src) SpinorIO<P>::load(src + (size_t)f * ld, (size_t)Vh, (size_t)k, p, inv, plo);
+    const R go = g5out ? R(-1) : R(1);
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) {
+        const R b = (sp < 2) ? beta * go : beta;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if constexpr (P == PDD) {
+                acc[sp][a].x = normalize(acc[sp][a].x);
+                acc[sp][a].y = normalize(acc[sp][a].y);
+            }
+            C v;
+            if (has_src) {
+                v.x = alpha * p[sp * 3 + a].x;
+                v.y = alpha * p[sp * 3 + a].y;
+                v.x = fma(b, acc[sp][a].x, v.x);
+                v.y = fma(b, acc[sp][a].y, v.y);
+            } else {
+                v.x = b * acc[sp][a].x;
+                v.y = b * acc[sp][a].y;
+            }
+            p[sp * 3 + a] = v;
+        }
+    }
+    SpinorIO<P>::store(out + (size_t)f * ld, (size_t)Vh, (size_t)k, p, scl, plo);
+}
+
 }  // namespace
 
 void launch_dslash(int prec, void* out, const void* in, size_t ld, const void* links, const Geom& g,
-                   double kappa, int g5in, int g5out, const Ctl* ctl, int nf_static, int nf_max,
-                   float hscale, cudaStream_t st) {
+                   double kappa, int dag, const Ctl* ctl, int nf_static, int nf_max, float hscale,
+                   cudaStream_t st) {
+    // D^H = gamma_5 D gamma_5: gamma_5 on the input and on the output
+    const int g5in = dag, g5out = dag;
     // one CTA per (field, 32-site tile); with a control block the width is
     // read on the device and bounded by nf_max, otherwise it is nf_static
     const int nfg = ctl ? nf_max : nf_static;
@@ -369,6 +500,27 @@ void launch_dslash(int prec, void* out, const void* in, size_t ld, const void* l
                                                          g5out, ctl, nf_static, hscale, nf_grid);
             break;
     }
+}
+
+void launch_dslash_half(int prec, void* out, const void* in, const void* src, size_t ld, const void* links,
+                        const Geom& g, double alpha, double beta, int parity, int g5in, int g5out, const Ctl* ctl,
+                        int nf_static, int nf_max, float hscale, cudaStream_t st) {
+    const int nfg = ctl ? nf_max : nf_static;
+    const int nf_grid = nfg < 1 ? 1 : nfg;
+    dim3 block(32);
+    dim3 grid((unsigned)(nf_grid * ((g.V / 2 + 31) / 32)));
+#define DSBCG_HALF_LAUNCH(PP, S2T, RA, RB)                                                                     \
+    dslash_half_kernel<PP><<<grid, block, 0, st>>>((S2T*)out, (const S2T*)in, (const S2T*)src, ld,            \
+                                                   (const S2T*)links, g, RA, RB, parity, g5in, g5out, ctl,    \
+                                                   nf_static, hscale, nf_grid)
+    switch (prec) {
+        case P64: DSBCG_HALF_LAUNCH(P64, double2, alpha, beta); break;
+        case P32: DSBCG_HALF_LAUNCH(P32, float2, (float)alpha, (float)beta); break;
+        case PBF16: DSBCG_HALF_LAUNCH(PBF16, __nv_bfloat162, (float)alpha, (float)beta); break;
+        case PF16: DSBCG_HALF_LAUNCH(PF16, __half2, (float)alpha, (float)beta); break;
+        case PDD: DSBCG_HALF_LAUNCH(PDD, float2, dd::from_double(alpha), dd::from_double(beta)); break;
+    }
+#undef DSBCG_HALF_LAUNCH
 }
 
 }  // namespace dsbcg

@@ -43,13 +43,35 @@ void launch_residual(double2* r, const double2* b, const double2* x, const doubl
                      int nblk, cudaStream_t st);
 int residual_blocks(size_t n);
 void launch_reduce_cols(const double* partials, int nblk, int m, double* out, cudaStream_t st);
+// Y (canonical complex128 [m][n]) = coef[0] B + sum_j coef[j+1] X_j from the
+// high-precision internal fields (hp = P64 or PDD) B [m] and X [s][m];
+// coef: device double[s + 1]
+void launch_rational_combine(int hp, double2* Y, const void* B, const void* X, size_t ld, int m, int s,
+                             const double* coef, size_t V, cudaStream_t st);
+// canonical complex128 blocks [s][cnt]: L_j *= w_j (w: host double[s], s <= S_MAX)
+void launch_scale_blocks(double2* L, int s, size_t cnt, const double* w, cudaStream_t st);
+// out[e] = a0 g[e] + sum_j L_j[e] (g unused when a0 = 0)
+void launch_sum_blocks(double2* out, const double2* L, int s, size_t cnt, const double2* g, double a0,
+                       cudaStream_t st);
+// out[j] = sum_e Re(conj(a_j[e]) b_j[e]) (device double[s]); partials: device double[s * nblk]
+void launch_dot_re_blocks(const double2* a, const double2* b, int s, size_t cnt, double* partials, int nblk,
+                          double* out, cudaStream_t st);
 
 // ---- dslash.cu ------------------------------------------------------------
-// out_f = D in_f (g5in/g5out wrap it with gamma_5) for fields f < nf,
-// where nf = ctl->mk when ctl != NULL, else nf_static.
+// out_f = D in_f (dag = 0) or D^H in_f = gamma_5 D gamma_5 in_f (dag = 1)
+// for fields f < nf, where nf = ctl->mk when ctl != NULL, else nf_static.
 void launch_dslash(int prec, void* out, const void* in, size_t ld, const void* links,
-                   const Geom& g, double kappa, int g5in, int g5out, const Ctl* ctl,
+                   const Geom& g, double kappa, int dag, const Ctl* ctl,
                    int nf_static, int nf_max, float hscale, cudaStream_t st);
+
+// Half-lattice hopping term of the even-odd operator (every extent even; half
+// fields of V / 2 sites, half index = canonical site / 2):
+// out_f = alpha src_f + beta G5o H G5i in_f, out and src on `parity`, in on
+// the other parity; src may be NULL (alpha ignored); G5i/G5o: gamma_5 on the
+// input / on the hopping term's output when g5in / g5out.
+void launch_dslash_half(int prec, void* out, const void* in, const void* src, size_t ld, const void* links,
+                        const Geom& g, double alpha, double beta, int parity, int g5in, int g5out, const Ctl* ctl,
+                        int nf_static, int nf_max, float hscale, cudaStream_t st);
 
 // ---- blas.cu ----------------------------------------------------------------
 int gram_blocks(size_t n, int nf_max);

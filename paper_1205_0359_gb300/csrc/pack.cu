@@ -217,6 +217,97 @@ __global__ void reduce_cols_kernel(const double* __restrict__ partials, int nblk
     }
 }
 
+// Y = coef[0] b + sum_j coef[j+1] x_j (canonical complex128 [m][n] out) from
+// high-precision internal fields: b = B[f], x_j = X[j m + f] (FP64, or
+// double-float hi + lo planes); FP64 arithmetic, shifts in index order
+template <int HP>
+__global__ void rational_combine_kernel(double2* __restrict__ Y, const void* __restrict__ Bv,
+                                        const void* __restrict__ Xv, size_t ld, int m, int s,
+                                        const double* __restrict__ coef, size_t V) {
+    const size_t n = 12 * V;
+    const size_t total = (size_t)m * n;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const size_t f = t / n, i = t % n;
+        const size_t e = fidx<P64>(V, i / 12, (int)(i % 12));
+        auto ld_hp = [&](const void* base, size_t field) -> double2 {
+            if constexpr (HP == P64) {
+                return reinterpret_cast<const double2*>(base)[field * ld + e];
+            } else {
+                const float2* q = reinterpret_cast<const float2*>(base) + field * 2 * ld + e;
+                const float2 h = q[0], l = q[ld];
+                return make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
+            }
+        };
+        const double2 b = ld_hp(Bv, f);
+        double ax = coef[0] * b.x, ay = coef[0] * b.y;
+        for (int j = 0; j < s; ++j) {
+            const double2 x = ld_hp(Xv, (size_t)j * m + f);
+            ax = fma(coef[j + 1], x.x, ax);
+            ay = fma(coef[j + 1], x.y, ay);
+        }
+        Y[t] = make_double2(ax, ay);
+    }
+}
+
+// ---- canonical complex128 blocks [s][cnt] of the backward pass
+
+struct ShiftWeights {
+    double w[S_MAX];
+};
+
+// L_j *= w_j for s blocks of cnt complex values
+__global__ void scale_blocks_kernel(double2* __restrict__ L, int s, size_t cnt, ShiftWeights w) {
+    const size_t total = (size_t)s * cnt;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const double a = w.w[t / cnt];
+        double2 v = L[t];
+        L[t] = make_double2(a * v.x, a * v.y);
+    }
+}
+
+// out = a0 g + sum_j L_j (shifts in index order; g may be NULL when a0 = 0)
+__global__ void sum_blocks_kernel(double2* __restrict__ out, const double2* __restrict__ L, int s, size_t cnt,
+                                  const double2* __restrict__ g, double a0) {
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < cnt; t += (size_t)gridDim.x * blockDim.x) {
+        double ax = 0.0, ay = 0.0;
+        if (g) {
+            const double2 v = g[t];
+            ax = a0 * v.x;
+            ay = a0 * v.y;
+        }
+        for (int j = 0; j < s; ++j) {
+            const double2 v = L[(size_t)j * cnt + t];
+            ax += v.x;
+            ay += v.y;
+        }
+        out[t] = make_double2(ax, ay);
+    }
+}
+
+// partials[j * nblk + b] = sum over CTA b's elements of Re(conj(a_j) b_j), grid (nblk, s)
+__global__ void dot_re_blocks_kernel(const double2* __restrict__ a, const double2* __restrict__ b, size_t cnt,
+                                     double* __restrict__ partials, int nblk) {
+    const int j = blockIdx.y;
+    const double2* aj = a + (size_t)j * cnt;
+    const double2* bj = b + (size_t)j * cnt;
+    double acc = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < cnt; i += (size_t)nblk * blockDim.x) {
+        const double2 u = aj[i], v = bj[i];
+        acc = fma(u.x, v.x, fma(u.y, v.y, acc));
+    }
+    __shared__ double red[RES_THREADS / 32];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < RES_THREADS / 32 ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) partials[(size_t)j * nblk + blockIdx.x] = v;
+    }
+}
+
 inline int grid_for(size_t total) {
     size_t g = (total + 255) / 256;
     if (g > 152 * 16) g = 152 * 16;
@@ -303,6 +394,33 @@ void launch_residual(double2* r, const double2* b, const double2* x, const doubl
 
 void launch_reduce_cols(const double* partials, int nblk, int m, double* out, cudaStream_t st) {
     reduce_cols_kernel<<<m, 256, 0, st>>>(partials, nblk, out);
+}
+
+void launch_rational_combine(int hp, double2* Y, const void* B, const void* X, size_t ld, int m, int s,
+                             const double* coef, size_t V, cudaStream_t st) {
+    const int g = grid_for((size_t)m * 12 * V);
+    if (hp == PDD)
+        rational_combine_kernel<PDD><<<g, 256, 0, st>>>(Y, B, X, ld, m, s, coef, V);
+    else
+        rational_combine_kernel<P64><<<g, 256, 0, st>>>(Y, B, X, ld, m, s, coef, V);
+}
+
+void launch_scale_blocks(double2* L, int s, size_t cnt, const double* w, cudaStream_t st) {
+    ShiftWeights sw;
+    for (int j = 0; j < S_MAX; ++j) sw.w[j] = j < s ? w[j] : 0.0;
+    scale_blocks_kernel<<<grid_for((size_t)s * cnt), 256, 0, st>>>(L, s, cnt, sw);
+}
+
+void launch_sum_blocks(double2* out, const double2* L, int s, size_t cnt, const double2* g, double a0,
+                       cudaStream_t st) {
+    sum_blocks_kernel<<<grid_for(cnt), 256, 0, st>>>(out, L, s, cnt, a0 != 0.0 ? g : nullptr, a0);
+}
+
+void launch_dot_re_blocks(const double2* a, const double2* b, int s, size_t cnt, double* partials, int nblk,
+                          double* out, cudaStream_t st) {
+    dim3 grid(nblk, s);
+    dot_re_blocks_kernel<<<grid, RES_THREADS, 0, st>>>(a, b, cnt, partials, nblk);
+    reduce_cols_kernel<<<s, 256, 0, st>>>(partials, nblk, out);
 }
 
 }  // namespace dsbcg

@@ -66,6 +66,7 @@ struct Lane {
     cudaStream_t st = nullptr;
     cudaEvent_t ready = nullptr;                  // own lanes: main-stream work they wait for
     void *vring = nullptr, *zw = nullptr, *y = nullptr, *P = nullptr, *Xin = nullptr;
+    void* eotmp = nullptr;                        // Schur operator: even-parity half fields
     double2* rhs = nullptr;                       // gathered right-hand sides (high precision)
     double* partials = nullptr;
     int nblk = 0;
@@ -90,6 +91,8 @@ struct Lane {
 struct dsbcg_ctx {
     Geom g;
     size_t V = 0, n = 0, ld = 0;
+    size_t Vf = 0;                       // sites of a field: V, or V / 2 for the Schur operator
+    int schur = 0;                       // 1: the even-odd Schur operator on the odd sites
     double kappa = 0;
     cudaStream_t st = nullptr;
     double2* gauge64 = nullptr;          // canonical copy of the links (device)
@@ -106,7 +109,10 @@ struct dsbcg_ctx {
     std::vector<void*> allocs;
     struct WS {
         int m = 0, s = 0, prec = -1;
+        int nbb = 0;                     // right-hand-side blocks in B64 (1, or s for per-shift B)
         void *vring = nullptr, *zw = nullptr, *y = nullptr;       // storage precision
+        void* eotmp = nullptr;                                    // Schur: even-parity half fields
+        double2* T64c = nullptr;                                  // Schur: high-precision half fields
         void *P = nullptr, *Xin = nullptr;                        // work precision
         double2 *B64 = nullptr, *X64 = nullptr, *R64 = nullptr, *T64a = nullptr, *T64b = nullptr, *rhs = nullptr;
         double2 *Xg = nullptr, *Bg = nullptr;
@@ -119,6 +125,7 @@ struct dsbcg_ctx {
         void *coef_a = nullptr, *coef_bh = nullptr, *coefS = nullptr, *coefU = nullptr, *coefL = nullptr;
         int *active = nullptr, *conv_step = nullptr;
         double *res = nullptr, *sigma = nullptr, *target = nullptr, *norms = nullptr;
+        double* coefR = nullptr;         // rational-combination weights alpha_0..alpha_s
         int* flag = nullptr;
         Ctl* h_ctl = nullptr;            // pinned
         double* h_norms = nullptr;       // pinned
@@ -228,9 +235,9 @@ dsbcg_status ensure_links(dsbcg_ctx* c, int prec) {
     return DSBCG_OK;
 }
 
-dsbcg_status ensure_ws(dsbcg_ctx* c, int m, int s, int prec) {
+dsbcg_status ensure_ws(dsbcg_ctx* c, int m, int s, int prec, int nbb) {
     auto& w = c->ws;
-    if (w.prec == prec && w.m >= m && w.s >= s && w.m == m) return DSBCG_OK;
+    if (w.prec == prec && w.m == m && w.s >= s && w.nbb >= nbb) return DSBCG_OK;
     free_ws(c);
     const size_t ld = c->ld, n = c->n;
     const size_t fb = prec_elem_bytes(prec) * ld;           // storage field bytes
@@ -240,9 +247,13 @@ dsbcg_status ensure_ws(dsbcg_ctx* c, int m, int s, int prec) {
     CKS(dmalloc(c, &w.vring, 2 * m * fb));
     CKS(dmalloc(c, &w.zw, m * fb));
     CKS(dmalloc(c, &w.y, m * fb));
+    if (c->schur) {
+        CKS(dmalloc(c, &w.eotmp, m * fb));
+        CKS(dmalloc(c, (void**)&w.T64c, m * db));
+    }
     CKS(dmalloc(c, (void**)&w.P, (size_t)s * m * wb));
     CKS(dmalloc(c, (void**)&w.Xin, (size_t)s * m * wb));
-    CKS(dmalloc(c, (void**)&w.B64, m * db));
+    CKS(dmalloc(c, (void**)&w.B64, (size_t)nbb * m * db));
     CKS(dmalloc(c, (void**)&w.X64, (size_t)s * m * db));
     CKS(dmalloc(c, (void**)&w.R64, m * db));
     CKS(dmalloc(c, (void**)&w.T64a, m * db));
@@ -272,6 +283,7 @@ dsbcg_status ensure_ws(dsbcg_ctx* c, int m, int s, int prec) {
     CKS(dmalloc(c, (void**)&w.sigma, s * sizeof(double)));
     CKS(dmalloc(c, (void**)&w.target, (size_t)s * m * sizeof(double)));
     CKS(dmalloc(c, (void**)&w.norms, (size_t)(s + 1) * m * sizeof(double)));
+    CKS(dmalloc(c, (void**)&w.coefR, (size_t)(s + 1) * sizeof(double)));
     CKS(dmalloc(c, (void**)&w.flag, sizeof(int)));
     CK(cudaMallocHost((void**)&w.h_ctl, sizeof(Ctl)));
     CK(cudaMallocHost((void**)&w.h_norms, (size_t)(s + 1) * m * sizeof(double)));
@@ -279,11 +291,13 @@ dsbcg_status ensure_ws(dsbcg_ctx* c, int m, int s, int prec) {
     w.m = m;
     w.s = s;
     w.prec = prec;
+    w.nbb = nbb;
     Lane L0;
     L0.st = c->st;
     L0.vring = w.vring;
     L0.zw = w.zw;
     L0.y = w.y;
+    L0.eotmp = w.eotmp;
     L0.P = w.P;
     L0.Xin = w.Xin;
     L0.rhs = w.rhs;
@@ -319,7 +333,7 @@ int ensure_refine_lanes(dsbcg_ctx* c, int want) {
     // a lane's buffers; lanes stop while a tenth of the device (at least
     // 4 GiB) would still be free, so that large lattices keep memory for the
     // caller
-    const size_t lane_bytes = 4 * m * fb + 2 * m * wb + m * db + gram_partial_doubles(M_MAX) * sizeof(double) +
+    const size_t lane_bytes = (c->schur ? 5 : 4) * m * fb + 2 * m * wb + m * db + gram_partial_doubles(M_MAX) * sizeof(double) +
                               small_state_bytes(1) + 6 * tb;
     while ((int)w.lanes.size() < want) {
         size_t fr = 0, tot = 0;
@@ -331,6 +345,7 @@ int ensure_refine_lanes(dsbcg_ctx* c, int want) {
         if (fr < lane_bytes + reserve) break;
         Lane L;
         bool ok = dmalloc(c, &L.vring, 2 * m * fb) == DSBCG_OK && dmalloc(c, &L.zw, m * fb) == DSBCG_OK &&
+                  (!c->schur || dmalloc(c, &L.eotmp, m * fb) == DSBCG_OK) &&
                   dmalloc(c, &L.y, m * fb) == DSBCG_OK && dmalloc(c, &L.P, m * wb) == DSBCG_OK &&
                   dmalloc(c, &L.Xin, m * wb) == DSBCG_OK && dmalloc(c, (void**)&L.rhs, m * db) == DSBCG_OK &&
                   dmalloc(c, (void**)&L.partials, gram_partial_doubles(M_MAX) * sizeof(double)) == DSBCG_OK &&
@@ -437,27 +452,62 @@ inline size_t hp_ld(const dsbcg_ctx* c, int hp) { return hp == PDD ? 2 * c->ld :
 // canonical complex128 fields <-> internal fields of any precision
 void pack_any(dsbcg_ctx* c, int p, void* dst, const double2* src, int m) {
     if (p == PDD)
-        launch_pack_pairs((float2*)dst, c->ld, src, m, c->V, c->st);
+        launch_pack_pairs((float2*)dst, c->ld, src, m, c->Vf, c->st);
     else
-        launch_pack_fields(p, dst, c->ld, src, m, c->V, c->hscale, c->st);
+        launch_pack_fields(p, dst, c->ld, src, m, c->Vf, c->hscale, c->st);
 }
 void unpack_any(dsbcg_ctx* c, int p, double2* dst, const void* src, int m) {
     if (p == PDD)
-        launch_unpack_pairs(dst, (const float2*)src, c->ld, m, c->V, c->st);
+        launch_unpack_pairs(dst, (const float2*)src, c->ld, m, c->Vf, c->st);
     else
-        launch_unpack_fields(p, dst, src, c->ld, m, c->V, c->hscale, c->st);
+        launch_unpack_fields(p, dst, src, c->ld, m, c->Vf, c->hscale, c->st);
 }
 
-// out = A in for nf high-precision fields (tmp receives D in)
+// out = Dhat in (dag = 0) or Dhat^H in (dag = 1) on odd-parity half fields,
+// Dhat = 1 - kappa^2 H_oe H_eo, Dhat^H = gamma_5 Dhat gamma_5; tmp receives
+// the even-parity H_eo (gamma_5) in.  Two half-lattice passes.
+void apply_dhat(dsbcg_ctx* c, int p, void* out, const void* in, void* tmp, size_t ld, int dag, const Ctl* ctl,
+                int nf_static, int nf_max, float hs, cudaStream_t st, int cls) {
+    {
+        Prof q(c, cls, 1, st);
+        launch_dslash_half(p, tmp, in, nullptr, ld, c->links[p], c->g, 0.0, 1.0, 0, dag, 0, ctl, nf_static, nf_max,
+                           hs, st);
+    }
+    {
+        Prof q(c, cls, 1, st);
+        launch_dslash_half(p, out, tmp, in, ld, c->links[p], c->g, 1.0, -c->kappa * c->kappa, 1, 0, dag, ctl,
+                           nf_static, nf_max, hs, st);
+    }
+}
+
+// out = Op in for the fields of a block in precision p: the normal operator
+// A = D^H D (two stencils; mid receives D in) or, on a context with the Schur
+// operator, Ahat = Dhat^H Dhat (four half-lattice passes; mid receives
+// Dhat in, tmp is scratch for even-parity half fields)
+void apply_op(dsbcg_ctx* c, int p, void* out, void* mid, const void* in, void* tmp, size_t ld, const Ctl* ctl,
+              int nf_static, int nf_max, float hs, cudaStream_t st, int cls) {
+    if (c->schur) {
+        apply_dhat(c, p, mid, in, tmp, ld, 0, ctl, nf_static, nf_max, hs, st, cls);
+        apply_dhat(c, p, out, mid, tmp, ld, 1, ctl, nf_static, nf_max, hs, st, cls);
+        return;
+    }
+    {
+        Prof q(c, cls, 1, st);
+        launch_dslash(p, mid, in, ld, c->links[p], c->g, c->kappa, 0, ctl, nf_static, nf_max, hs, st);
+    }
+    {
+        Prof q(c, cls, 1, st);
+        launch_dslash(p, out, mid, ld, c->links[p], c->g, c->kappa, 1, ctl, nf_static, nf_max, hs, st);
+    }
+}
+
+// link passes of one operator application: 2 (A) or 4 (Ahat); each pass
+// reads every link once
+inline double link_passes(const dsbcg_ctx* c) { return c->schur ? 4.0 : 2.0; }
+
+// out = A in (or Ahat in) for nf high-precision fields (tmp receives D in)
 void apply_Ahp(dsbcg_ctx* c, int hp, void* out, const void* in, void* tmp, int nf) {
-    {
-        Prof p(c, DSBCG_KCLASS_RESIDUAL);
-        launch_dslash(hp, tmp, in, hp_ld(c, hp), c->links[hp], c->g, c->kappa, 0, 0, nullptr, nf, nf, 1.f, c->st);
-    }
-    {
-        Prof p(c, DSBCG_KCLASS_RESIDUAL);
-        launch_dslash(hp, out, tmp, hp_ld(c, hp), c->links[hp], c->g, c->kappa, 1, 1, nullptr, nf, nf, 1.f, c->st);
-    }
+    apply_op(c, hp, out, tmp, in, c->ws.T64c, hp_ld(c, hp), nullptr, nf, nf, 1.f, c->st, DSBCG_KCLASS_RESIDUAL);
 }
 
 // r = b - sigma x - A x for m high-precision fields; squared column norms
@@ -478,7 +528,7 @@ dsbcg_status true_residual(dsbcg_ctx* c, int hp, double2* r, const double2* b, c
     }
     // two stencils (m fields in and out, links once each) + b, x, Ax in, r out
     c->kbytes[DSBCG_KCLASS_RESIDUAL] +=
-        (8.0 * m * c->n + 2.0 * 36 * c->V) * sizeof(double2);
+        ((c->schur ? 14.0 : 8.0) * m * c->n + link_passes(c) * 36 * c->V) * sizeof(double2);
     CK(cudaMemcpyAsync(w.h_norms, w.norms, m * sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     for (int i = 0; i < m; ++i) h_out[i] = w.h_norms[i];
@@ -557,14 +607,7 @@ dsbcg_status lane_enqueue(dsbcg_ctx* c, Lane& L) {
         const int step = ++L.step;
         void* Vk = ring + (size_t)(step % 2) * m_in * fb;
         void* Vo = ring + (size_t)((step + 1) % 2) * m_in * fb;     // V_{k-1}, then V_{k+1}
-        {
-            Prof p(c, DSBCG_KCLASS_DSLASH, 1, st);
-            launch_dslash(prec, L.zw, Vk, ld, c->links[prec], c->g, c->kappa, 0, 0, L.ctl, 0, m_in, c->hscale, st);
-        }
-        {
-            Prof p(c, DSBCG_KCLASS_DSLASH, 1, st);
-            launch_dslash(prec, L.y, L.zw, ld, c->links[prec], c->g, c->kappa, 1, 1, L.ctl, 0, m_in, c->hscale, st);
-        }
+        apply_op(c, prec, L.y, L.zw, Vk, L.eotmp, ld, L.ctl, 0, m_in, c->hscale, st, DSBCG_KCLASS_DSLASH);
         {
             Prof p(c, DSBCG_KCLASS_GRAM, 1, st);
             launch_gram(prec, Vk, L.y, ld, n, L.ctl, 0, m_in, 0, 1, L.partials, L.nblk, c->hscale, st);
@@ -639,7 +682,9 @@ dsbcg_status lane_finish(dsbcg_ctx* c, Lane& L, InnerResult* out, int step_offse
     {
         const double eb = (double)prec_elem_bytes(prec) * n, wbn = (double)prec_elem_bytes(wp) * n;
         const double links = 36.0 * c->V * (double)prec_elem_bytes(prec);
-        c->kbytes[DSBCG_KCLASS_DSLASH] += h.f_dslash * eb + 2.0 * h.last_step * links;
+        // the Schur operator's four passes move 10 half fields per block
+        // column (the counter counts the normal operator's 4)
+        c->kbytes[DSBCG_KCLASS_DSLASH] += h.f_dslash * eb * (c->schur ? 2.5 : 1.0) + link_passes(c) * h.last_step * links;
         c->kbytes[DSBCG_KCLASS_GRAM] += h.f_gram * eb;
         c->kbytes[DSBCG_KCLASS_UPDATE] += h.f_update * eb;
         c->kbytes[DSBCG_KCLASS_SHIFT] += h.f_shift_s * eb + h.f_shift_w * wbn;
@@ -665,193 +710,32 @@ double default_dtol(int prec) {
 }  // namespace
 
 // ============================================================================
-extern "C" {
+namespace {
 
-void dsbcg_params_default(dsbcg_params* p) {
-    if (!p) return;
-    p->storage = DSBCG_PREC_FP32;
-    p->dtol = 0.0;
-    p->max_block_steps = 100000;
-    p->max_restarts = 50;
-    p->restart_drop = 1e-6;
-    p->poll_every = 16;
-    p->freeze_converged = 1;
-    p->refine = 1;
-    p->fp64_residuals = 0;
-    p->x0 = 0;
-}
+// The solve behind dsbcg_solve, dsbcg_solve_rational and the adjoint solves of
+// dsbcg_backward.  nbb = 1: one block B [m][n] for every shift (the joint
+// block solve of Sec. 3 first); nbb = s: B is [s][m][n], shift j's own
+// right-hand sides (each shift solved on a refinement lane, no joint solve).
+// X (caller's [s][m][n]) may be NULL when rat is set; rat writes
+// Y = alpha_0 B + sum_j alpha_j X_j (single-block B only).
+struct RationalOut {
+    double alpha0;
+    const double* alpha;     // host [s]
+    void* Y;                 // device or host complex128 [m][n]
+};
 
-const char* dsbcg_error_string(dsbcg_status s) {
-    switch (s) {
-        case DSBCG_OK: return "ok";
-        case DSBCG_NOT_CONVERGED: return "not converged (iteration or restart cap reached)";
-        case DSBCG_ERR_ARG: return "invalid argument";
-        case DSBCG_ERR_NOT_HPD: return "sigma_j I + T is not hermitian positive definite";
-        case DSBCG_ERR_CUDA: return "CUDA runtime error";
-        case DSBCG_ERR_OOM: return "device out of memory";
-        case DSBCG_ERR_NONFINITE: return "non-finite input";
-        case DSBCG_ERR_UNSUPPORTED: return "unsupported option";
-    }
-    return "unknown status";
-}
-
-const char* dsbcg_version(void) { return "dsbcg 0.1 sm_103a"; }
-
-dsbcg_status dsbcg_create(dsbcg_ctx** out, const int dims[4], const void* gauge, double kappa, int t_antiperiodic,
-                          void* stream) {
-    if (!out || !dims || !gauge) return DSBCG_ERR_ARG;
-    *out = nullptr;
-    for (int d = 0; d < 4; ++d)
-        if (dims[d] < 2 || dims[d] > 4096) return DSBCG_ERR_ARG;
-    if (!(kappa == kappa) || !isfinite(kappa)) return DSBCG_ERR_ARG;
-    size_t V = (size_t)dims[0] * dims[1] * dims[2] * dims[3];
-    if (V > (size_t)1 << 30) return DSBCG_ERR_ARG;
-    dsbcg_ctx* c = new dsbcg_ctx();
-    for (int d = 0; d < 4; ++d) c->g.L[d] = dims[d];
-    c->g.V = (int)V;
-    c->g.tap = t_antiperiodic ? 1 : 0;
-    c->V = V;
-    c->n = 12 * V;
-    c->ld = (c->n + 127) / 128 * 128;
-    c->kappa = kappa;
-    c->st = (cudaStream_t)stream;
-    // 16-bit scale: power of two near sqrt(n)
-    c->hscale = (float)ldexp(1.0, (int)lround(0.5 * log2((double)c->n)));
-    dsbcg_status st = dsbcg_update_gauge(c, gauge);
-    if (st != DSBCG_OK) {
-        dsbcg_destroy(c);
-        return st;
-    }
-    *out = c;
-    return DSBCG_OK;
-}
-
-dsbcg_status dsbcg_update_gauge(dsbcg_ctx* c, const void* gauge) {
-    if (!c || !gauge) return DSBCG_ERR_ARG;
-    // From here until the new field has been checked and packed the context
-    // holds no usable field: the old packed links go first, so that no
-    // precision keeps links of the old field while gauge64 holds the new one.
-    c->gauge_ok = false;
-    for (int p = 0; p < 5; ++p) {
-        if (c->links[p]) {
-            cudaFree(c->links[p]);
-            c->links[p] = nullptr;
-        }
-    }
-    const size_t bytes = c->V * 36 * sizeof(double2);
-    if (!c->gauge64) CK(cudaMalloc((void**)&c->gauge64, bytes));
-    CK(cudaMemcpyAsync(c->gauge64, gauge, bytes, is_device_ptr(gauge) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                       c->st));
-    int* flag = nullptr;
-    CK(cudaMalloc((void**)&flag, sizeof(int)));
-    cudaMemsetAsync(flag, 0, sizeof(int), c->st);
-    launch_check_finite(c->gauge64, c->V * 36, flag, c->st);
-    int h = 0;
-    cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, c->st);
-    const cudaError_t e = cudaStreamSynchronize(c->st);
-    cudaFree(flag);
-    CK(e);
-    if (h) return DSBCG_ERR_NONFINITE;
-    CKS(ensure_links(c, P64));
-    c->gauge_ok = true;
-    return DSBCG_OK;
-}
-
-void dsbcg_destroy(dsbcg_ctx* c) {
-    if (!c) return;
-    free_ws(c);
-    for (int p = 0; p < 5; ++p)
-        if (c->links[p]) cudaFree(c->links[p]);
-    if (c->gauge64) cudaFree(c->gauge64);
-    for (auto e : c->ev_pool) cudaEventDestroy(e);
-    for (auto& k : c->ev_live) {
-        cudaEventDestroy(k.a);
-        cudaEventDestroy(k.b);
-    }
-    delete c;
-}
-
-dsbcg_status dsbcg_set_profiling(dsbcg_ctx* c, int on) {
-    if (!c) return DSBCG_ERR_ARG;
-    c->profiling = on != 0;
-    return DSBCG_OK;
-}
-
-dsbcg_status dsbcg_read_profile(dsbcg_ctx* c, double kernel_ms[8], long long kernel_launches[8]) {
-    if (!c) return DSBCG_ERR_ARG;
-    CK(cudaStreamSynchronize(c->st));
-    prof_collect(c);
-    for (int q = 0; q < 8; ++q) {
-        if (kernel_ms) kernel_ms[q] = c->kms[q];
-        if (kernel_launches) kernel_launches[q] = c->klaunch[q];
-        c->kms[q] = 0;
-        c->klaunch[q] = 0;
-        c->kbytes[q] = 0;
-    }
-    return DSBCG_OK;
-}
-
-dsbcg_status dsbcg_apply(dsbcg_ctx* c, int op, int storage, int m, const void* in, void* out) {
-    if (!c || !in || !out || m < 1 || m > 4096 || op < 0 || op > 2 || storage < 0 || storage > PDD)
-        return DSBCG_ERR_ARG;
-    if (!c->gauge_ok) return DSBCG_ERR_ARG;
-    CKS(ensure_links(c, storage));
-    const size_t n = c->n, ld = hp_ld(c, storage);
-    const size_t fb = prec_elem_bytes(storage) * c->ld;
-    void *a = nullptr, *b = nullptr, *t = nullptr;
-    double2 *din = nullptr, *dout = nullptr;
-    const bool in_dev = is_device_ptr(in), out_dev = is_device_ptr(out);
-    dsbcg_status rs = DSBCG_OK;
-    auto fail = [&](dsbcg_status s) { rs = s; };
-    if (cudaMalloc(&a, m * fb) != cudaSuccess || cudaMalloc(&b, m * fb) != cudaSuccess ||
-        cudaMalloc(&t, m * fb) != cudaSuccess) {
-        fail(DSBCG_ERR_OOM);
-    }
-    if (rs == DSBCG_OK && !in_dev) {
-        if (cudaMalloc((void**)&din, m * n * sizeof(double2)) != cudaSuccess) fail(DSBCG_ERR_OOM);
-        else cudaMemcpyAsync(din, in, m * n * sizeof(double2), cudaMemcpyHostToDevice, c->st);
-    }
-    if (rs == DSBCG_OK && !out_dev) {
-        if (cudaMalloc((void**)&dout, m * n * sizeof(double2)) != cudaSuccess) fail(DSBCG_ERR_OOM);
-    }
-    if (rs == DSBCG_OK) {
-        const double2* src = in_dev ? (const double2*)in : din;
-        double2* dst = out_dev ? (double2*)out : dout;
-        pack_any(c, storage, a, src, m);
-        if (op == DSBCG_OP_D) {
-            Prof p(c, DSBCG_KCLASS_DSLASH);
-            launch_dslash(storage, b, a, ld, c->links[storage], c->g, c->kappa, 0, 0, nullptr, m, m, c->hscale, c->st);
-        } else if (op == DSBCG_OP_DDAG) {
-            Prof p(c, DSBCG_KCLASS_DSLASH);
-            launch_dslash(storage, b, a, ld, c->links[storage], c->g, c->kappa, 1, 1, nullptr, m, m, c->hscale, c->st);
-        } else {
-            {
-                Prof p(c, DSBCG_KCLASS_DSLASH);
-                launch_dslash(storage, t, a, ld, c->links[storage], c->g, c->kappa, 0, 0, nullptr, m, m, c->hscale,
-                              c->st);
-            }
-            Prof p(c, DSBCG_KCLASS_DSLASH);
-            launch_dslash(storage, b, t, ld, c->links[storage], c->g, c->kappa, 1, 1, nullptr, m, m, c->hscale, c->st);
-        }
-        unpack_any(c, storage, dst, b, m);
-        if (!out_dev) cudaMemcpyAsync(out, dout, m * n * sizeof(double2), cudaMemcpyDeviceToHost, c->st);
-        if (cudaGetLastError() != cudaSuccess) fail(DSBCG_ERR_CUDA);
-        if (cudaStreamSynchronize(c->st) != cudaSuccess) fail(DSBCG_ERR_CUDA);
-        prof_collect(c);
-    }
-    cudaFree(a);
-    cudaFree(b);
-    cudaFree(t);
-    if (din) cudaFree(din);
-    if (dout) cudaFree(dout);
-    return rs;
-}
-
-dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double* sigma, double tol,
-                         const dsbcg_params* params, void* X, dsbcg_stats* stats) {
+dsbcg_status solve_core(dsbcg_ctx* c, int m, const void* B, int nbb, int s, const double* sigma, double tol,
+                        const dsbcg_params* params, void* X, dsbcg_stats* stats, const RationalOut* rat) {
     Range r_solve("dsbcg_solve");
     auto t0 = std::chrono::steady_clock::now();
-    if (!c || !B || !X || !sigma || m < 1 || m > M_MAX || s < 1 || s > S_MAX) return DSBCG_ERR_ARG;
+    if (!c || !B || !sigma || m < 1 || m > M_MAX || s < 1 || s > S_MAX) return DSBCG_ERR_ARG;
+    if (!X && !rat) return DSBCG_ERR_ARG;
+    if (nbb != 1 && (nbb != s || rat)) return DSBCG_ERR_ARG;
+    if (rat) {
+        if (!rat->Y || !rat->alpha || !isfinite(rat->alpha0)) return DSBCG_ERR_ARG;
+        for (int j = 0; j < s; ++j)
+            if (!isfinite(rat->alpha[j])) return DSBCG_ERR_ARG;
+    }
     if (!c->gauge_ok) return DSBCG_ERR_ARG;
     if (!(tol >= 0.0) || !isfinite(tol)) return DSBCG_ERR_ARG;
     for (int j = 0; j < s; ++j)
@@ -862,6 +746,7 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
     const int prec = prm.storage;
     if (prec < 0 || prec > 3) return DSBCG_ERR_ARG;
     if (prm.poll_every < 1) prm.poll_every = 1;
+    if (prm.x0 && !X) return DSBCG_ERR_ARG;
     const double dtol = prm.dtol > 0 ? prm.dtol : default_dtol(prec);
     const bool mixed = prec != P64;
     // true residuals, B and the accumulated solutions: FP64 fields for FP64
@@ -871,7 +756,7 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
     const int hp = sfp64 ? P64 : PDD;
     CKS(ensure_links(c, prec));
     CKS(ensure_links(c, hp));
-    CKS(ensure_ws(c, m, s, prec));
+    CKS(ensure_ws(c, m, s, prec, nbb));
     auto& w = c->ws;
     const size_t n = c->n, ld = c->ld;
     const size_t db = ld * sizeof(double2);
@@ -882,44 +767,49 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
     }
 
     // --- inputs: B -> internal high-precision fields (staging through X64's storage if on the host)
-    const bool b_dev = is_device_ptr(B), x_dev = is_device_ptr(X);
+    const bool b_dev = is_device_ptr(B), x_dev = X && is_device_ptr(X);
+    const size_t nb_fields = (size_t)nbb * m;
     double2* bcanon = nullptr;
     if (b_dev) {
         bcanon = (double2*)B;
     } else if (void* bmap = mapped_host_ptr(B)) {
         bcanon = (double2*)bmap;   // pinned and mapped: the kernels read it in place
     } else {
-        bcanon = w.X64;        // X64 has >= m*ld complex; used as staging before it is zeroed
-        CK(cudaMemcpyAsync(bcanon, B, (size_t)m * n * sizeof(double2), cudaMemcpyHostToDevice, c->st));
+        bcanon = w.X64;        // X64 has >= nbb*m*ld complex; used as staging before it is zeroed
+        CK(cudaMemcpyAsync(bcanon, B, nb_fields * n * sizeof(double2), cudaMemcpyHostToDevice, c->st));
     }
     CK(cudaMemsetAsync(w.flag, 0, sizeof(int), c->st));
     {
         Prof p(c, DSBCG_KCLASS_OTHER, 2);
-        launch_check_finite(bcanon, (size_t)m * n, w.flag, c->st);
-        pack_any(c, hp, w.B64, bcanon, m);
+        launch_check_finite(bcanon, nb_fields * n, w.flag, c->st);
+        pack_any(c, hp, w.B64, bcanon, (int)nb_fields);
     }
     int hflag = 0;
     CK(cudaMemcpyAsync(&hflag, w.flag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     CK(cudaMemsetAsync(w.X64, 0, (size_t)s * m * db, c->st));
-    // ||b_i||^2 via the residual kernel with x = 0 (A 0 = 0)
-    std::vector<double> bn2(m), bn(m);
+    // ||b_i||^2 via the residual kernel with x = 0 (A 0 = 0), per block of B
+    std::vector<double> bn2(nb_fields), bn(nb_fields);
     {
-        {
+        for (int jb = 0; jb < nbb; ++jb) {
             Prof p(c, DSBCG_KCLASS_OTHER, 2);
+            const double2* bj = w.B64 + (size_t)jb * m * ld;
             if (hp == PDD)
-                launch_residual_pairs((float2*)w.R64, (const float2*)w.B64, (const float2*)w.X64,
+                launch_residual_pairs((float2*)w.R64, (const float2*)bj, (const float2*)w.X64,
                                       (const float2*)w.X64, ld, m, n, 0.0, w.rpart, w.rblk, c->st);
             else
-                launch_residual(w.R64, w.B64, w.X64, w.X64, ld, m, n, 0.0, w.rpart, w.rblk, c->st);
-            launch_reduce_cols(w.rpart, w.rblk, m, w.norms, c->st);
+                launch_residual(w.R64, bj, w.X64, w.X64, ld, m, n, 0.0, w.rpart, w.rblk, c->st);
+            launch_reduce_cols(w.rpart, w.rblk, m, w.norms + (size_t)jb * m, c->st);
         }
-        CK(cudaMemcpyAsync(w.h_norms, w.norms, m * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaMemcpyAsync(w.h_norms, w.norms, nb_fields * sizeof(double), cudaMemcpyDeviceToHost, c->st));
         CK(cudaStreamSynchronize(c->st));
-        for (int i = 0; i < m; ++i) {
+        for (size_t i = 0; i < nb_fields; ++i) {
             bn2[i] = w.h_norms[i];
             bn[i] = sqrt(bn2[i]);
         }
     }
+    // right-hand sides and their norms for shift j
+    auto Bblk = [&](int j) { return w.B64 + (size_t)(nbb > 1 ? j : 0) * m * ld; };
+    auto bnorm = [&](int j, int i) { return bn[(size_t)(nbb > 1 ? j : 0) * m + i]; };
     if (hflag) return DSBCG_ERR_NONFINITE;
     // --- initial guess (a resumed solve): X's input, packed shift by shift
     // into the high-precision X_j (the norms above were taken with X = 0)
@@ -966,9 +856,13 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
     };
     const double drop = mixed ? std::max(prm.restart_drop, 1e-12) : 0.0;
 
-    // --- joint inner solve on B for all shifts (not with an initial guess:
-    // the shifts' residuals then differ, and each is restarted on its own)
-    if (!prm.x0) {
+    // --- joint inner solve on B for all shifts (not with an initial guess or
+    // per-shift right-hand sides: the shifts' residuals then differ, and each
+    // is restarted on its own)
+    // shifts whose X_j is still zero (per-shift right-hand sides): their
+    // first residual is b itself, no operator application needed
+    std::vector<char> xzero(s, (nbb > 1 && !prm.x0) ? 1 : 0);
+    if (!prm.x0 && nbb == 1) {
         Range r_joint("joint block solve");
         std::vector<double> tg((size_t)s * m);
         for (int j = 0; j < s; ++j)
@@ -991,7 +885,7 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
     // soon as its last true residual is in (device or mapped pinned host
     // memory; other host memory is staged at the end), so that the transfer
     // overlaps the restarts of the other shifts
-    void* const xmap = x_dev ? nullptr : mapped_host_ptr(X);
+    void* const xmap = (x_dev || !X) ? nullptr : mapped_host_ptr(X);
     double2* const xout = x_dev ? (double2*)X : (double2*)xmap;
     auto emit = [&](int j) {
         if (!xout) return;
@@ -1041,21 +935,33 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
             queue.pop_front();
             double2* Xj = w.X64 + (size_t)j * m * ld;
             std::vector<int>& cl = cols[j];
-            if (full[j]) {
+            if (full[j] && xzero[j]) {
+                // X_j = 0: the residual is b_j itself
+                cl.resize(m);
+                for (int i = 0; i < m; ++i) {
+                    cl[i] = i;
+                    r2[i] = bnorm(j, i) * bnorm(j, i);
+                }
+                CK(cudaMemcpyAsync(w.R64, Bblk(j), (size_t)m * db, cudaMemcpyDeviceToDevice, c->st));
+                full[j] = 0;
+                xzero[j] = 0;
+            } else if (full[j]) {
                 cl.resize(m);
                 for (int i = 0; i < m; ++i) cl[i] = i;
-                CKS(true_residual(c, hp, w.R64, w.B64, Xj, m, sigma[j], r2.data()));
+                CKS(true_residual(c, hp, w.R64, Bblk(j), Xj, m, sigma[j], r2.data()));
                 full[j] = 0;
+                mvms += (long long)cl.size();
             } else {
                 CKS(gather(w.Xg, Xj, cl));
-                CKS(gather(w.Bg, w.B64, cl));
+                CKS(gather(w.Bg, Bblk(j), cl));
                 CKS(true_residual(c, hp, w.R64, w.Bg, w.Xg, (int)cl.size(), sigma[j], r2.data()));
+                mvms += (long long)cl.size();
             }
-            mvms += (long long)cl.size();
             std::vector<int> next, src;        // unconverged columns; their rows of R64
             for (size_t q = 0; q < cl.size(); ++q) {
                 const int i = cl[q];
-                rel[(size_t)j * m + i] = bn[i] > 0 ? sqrt(r2[q]) / bn[i] : 0.0;
+                const double bi = bnorm(j, i);
+                rel[(size_t)j * m + i] = bi > 0 ? sqrt(r2[q]) / bi : 0.0;
                 if (rel[(size_t)j * m + i] > tol) {
                     next.push_back(i);
                     src.push_back((int)q);
@@ -1072,7 +978,7 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
             tg.resize(mu);
             for (int q = 0; q < mu; ++q) {
                 const int i = cl[q];
-                tg[q] = std::max(drop * rel[(size_t)j * m + i] * bn[i], 0.5 * tol * bn[i]);
+                tg[q] = std::max(drop * rel[(size_t)j * m + i] * bnorm(j, i), 0.5 * tol * bnorm(j, i));
             }
             CKS(gather(L.rhs, w.R64, src));
             if (L.st != c->st) {
@@ -1132,7 +1038,25 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
         Prof p(c, DSBCG_KCLASS_OTHER);
         unpack_any(c, hp, dst, src, nf);
     };
-    if (xout) {
+    if (rat) {
+        // Y = alpha_0 B + sum_j alpha_j X_j in one pass over the final
+        // solutions, shifts summed in index order (bitwise reproducible)
+        std::vector<double> coef(s + 1);
+        coef[0] = rat->alpha0;
+        for (int j = 0; j < s; ++j) coef[j + 1] = rat->alpha[j];
+        CK(cudaMemcpyAsync(w.coefR, coef.data(), (s + 1) * sizeof(double), cudaMemcpyHostToDevice, c->st));
+        const bool y_dev = is_device_ptr(rat->Y);
+        void* ymap = y_dev ? nullptr : mapped_host_ptr(rat->Y);
+        double2* ydst = y_dev ? (double2*)rat->Y : (ymap ? (double2*)ymap : w.T64a);
+        {
+            Prof p(c, DSBCG_KCLASS_OTHER);
+            launch_rational_combine(hp, ydst, w.B64, w.X64, ld, m, s, w.coefR, c->Vf, c->st);
+        }
+        c->kbytes[DSBCG_KCLASS_OTHER] += (double)(s + 1) * m * n * 16.0 + (double)m * n * 16.0;
+        if (!y_dev && !ymap)
+            CK(cudaMemcpyAsync(rat->Y, w.T64a, (size_t)m * n * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
+    }
+    if (xout || !X) {
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(c->st));
     } else {
@@ -1163,11 +1087,223 @@ dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double
     return result;
 }
 
+}  // namespace
+
+
+extern "C" {
+
+void dsbcg_params_default(dsbcg_params* p) {
+    if (!p) return;
+    p->storage = DSBCG_PREC_FP32;
+    p->dtol = 0.0;
+    p->max_block_steps = 100000;
+    p->max_restarts = 50;
+    p->restart_drop = 1e-6;
+    p->poll_every = 16;
+    p->freeze_converged = 1;
+    p->refine = 1;
+    p->fp64_residuals = 1;
+    p->x0 = 0;
+}
+
+const char* dsbcg_error_string(dsbcg_status s) {
+    switch (s) {
+        case DSBCG_OK: return "ok";
+        case DSBCG_NOT_CONVERGED: return "not converged (iteration or restart cap reached)";
+        case DSBCG_ERR_ARG: return "invalid argument";
+        case DSBCG_ERR_NOT_HPD: return "sigma_j I + T is not hermitian positive definite";
+        case DSBCG_ERR_CUDA: return "CUDA runtime error";
+        case DSBCG_ERR_OOM: return "device out of memory";
+        case DSBCG_ERR_NONFINITE: return "non-finite input";
+        case DSBCG_ERR_UNSUPPORTED: return "unsupported option";
+    }
+    return "unknown status";
+}
+
+const char* dsbcg_version(void) { return "dsbcg 0.1 sm_103a"; }
+
+dsbcg_status dsbcg_create(dsbcg_ctx** out, const int dims[4], const void* gauge, double kappa, int t_antiperiodic,
+                          void* stream) {
+    if (!out || !dims || !gauge) return DSBCG_ERR_ARG;
+    *out = nullptr;
+    for (int d = 0; d < 4; ++d)
+        if (dims[d] < 2 || dims[d] > 4096) return DSBCG_ERR_ARG;
+    if (!(kappa == kappa) || !isfinite(kappa)) return DSBCG_ERR_ARG;
+    size_t V = (size_t)dims[0] * dims[1] * dims[2] * dims[3];
+    if (V > (size_t)1 << 30) return DSBCG_ERR_ARG;
+    dsbcg_ctx* c = new dsbcg_ctx();
+    for (int d = 0; d < 4; ++d) c->g.L[d] = dims[d];
+    c->g.V = (int)V;
+    c->g.tap = t_antiperiodic ? 1 : 0;
+    c->V = V;
+    c->Vf = V;
+    c->n = 12 * V;
+    c->ld = (c->n + 127) / 128 * 128;
+    c->kappa = kappa;
+    c->st = (cudaStream_t)stream;
+    // 16-bit scale: power of two near sqrt(n)
+    c->hscale = (float)ldexp(1.0, (int)lround(0.5 * log2((double)c->n)));
+    dsbcg_status st = dsbcg_update_gauge(c, gauge);
+    if (st != DSBCG_OK) {
+        dsbcg_destroy(c);
+        return st;
+    }
+    *out = c;
+    return DSBCG_OK;
+}
+
+dsbcg_status dsbcg_update_gauge(dsbcg_ctx* c, const void* gauge) {
+    if (!c || !gauge) return DSBCG_ERR_ARG;
+    // From here until the new field has been checked and packed the context
+    // holds no usable field: the old packed links go first, so that no
+    // precision keeps links of the old field while gauge64 holds the new one.
+    c->gauge_ok = false;
+    for (int p = 0; p < 5; ++p) {
+        if (c->links[p]) {
+            cudaFree(c->links[p]);
+            c->links[p] = nullptr;
+        }
+    }
+    const size_t bytes = c->V * 36 * sizeof(double2);
+    if (!c->gauge64) CK(cudaMalloc((void**)&c->gauge64, bytes));
+    CK(cudaMemcpyAsync(c->gauge64, gauge, bytes, is_device_ptr(gauge) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       c->st));
+    int* flag = nullptr;
+    CK(cudaMalloc((void**)&flag, sizeof(int)));
+    cudaMemsetAsync(flag, 0, sizeof(int), c->st);
+    launch_check_finite(c->gauge64, c->V * 36, flag, c->st);
+    int h = 0;
+    cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+    const cudaError_t e = cudaStreamSynchronize(c->st);
+    cudaFree(flag);
+    CK(e);
+    if (h) return DSBCG_ERR_NONFINITE;
+    CKS(ensure_links(c, P64));
+    c->gauge_ok = true;
+    return DSBCG_OK;
+}
+
+dsbcg_status dsbcg_solve(dsbcg_ctx* c, int m, const void* B, int s, const double* sigma, double tol,
+                         const dsbcg_params* params, void* X, dsbcg_stats* stats) {
+    if (!X) return DSBCG_ERR_ARG;
+    return solve_core(c, m, B, 1, s, sigma, tol, params, X, stats, nullptr);
+}
+
+dsbcg_status dsbcg_solve_rational(dsbcg_ctx* c, int m, const void* B, int s, const double* sigma, double alpha0,
+                                  const double* alpha, double tol, const dsbcg_params* params, void* Y, void* X,
+                                  dsbcg_stats* stats) {
+    if (!Y || !alpha) return DSBCG_ERR_ARG;
+    const RationalOut r{alpha0, alpha, Y};
+    return solve_core(c, m, B, 1, s, sigma, tol, params, X, stats, &r);
+}
+
+void dsbcg_destroy(dsbcg_ctx* c) {
+    if (!c) return;
+    free_ws(c);
+    for (int p = 0; p < 5; ++p)
+        if (c->links[p]) cudaFree(c->links[p]);
+    if (c->gauge64) cudaFree(c->gauge64);
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    for (auto& k : c->ev_live) {
+        cudaEventDestroy(k.a);
+        cudaEventDestroy(k.b);
+    }
+    delete c;
+}
+
+dsbcg_status dsbcg_set_profiling(dsbcg_ctx* c, int on) {
+    if (!c) return DSBCG_ERR_ARG;
+    c->profiling = on != 0;
+    return DSBCG_OK;
+}
+
+dsbcg_status dsbcg_read_profile(dsbcg_ctx* c, double kernel_ms[8], long long kernel_launches[8]) {
+    if (!c) return DSBCG_ERR_ARG;
+    CK(cudaStreamSynchronize(c->st));
+    prof_collect(c);
+    for (int q = 0; q < 8; ++q) {
+        if (kernel_ms) kernel_ms[q] = c->kms[q];
+        if (kernel_launches) kernel_launches[q] = c->klaunch[q];
+        c->kms[q] = 0;
+        c->klaunch[q] = 0;
+        c->kbytes[q] = 0;
+    }
+    return DSBCG_OK;
+}
+
+dsbcg_status dsbcg_apply(dsbcg_ctx* c, int op, int storage, int m, const void* in, void* out) {
+    if (!c || !in || !out || m < 1 || m > 4096 || op < 0 || op > 2 || storage < 0 || storage > PDD)
+        return DSBCG_ERR_ARG;
+    if (!c->gauge_ok) return DSBCG_ERR_ARG;
+    CKS(ensure_links(c, storage));
+    const size_t n = c->n, ld = hp_ld(c, storage);
+    const size_t fb = prec_elem_bytes(storage) * c->ld;
+    void *a = nullptr, *b = nullptr, *t = nullptr, *t2 = nullptr;
+    double2 *din = nullptr, *dout = nullptr;
+    const bool in_dev = is_device_ptr(in), out_dev = is_device_ptr(out);
+    dsbcg_status rs = DSBCG_OK;
+    auto fail = [&](dsbcg_status s) { rs = s; };
+    if (cudaMalloc(&a, m * fb) != cudaSuccess || cudaMalloc(&b, m * fb) != cudaSuccess ||
+        cudaMalloc(&t, m * fb) != cudaSuccess || (c->schur && cudaMalloc(&t2, m * fb) != cudaSuccess)) {
+        fail(DSBCG_ERR_OOM);
+    }
+    if (rs == DSBCG_OK && !in_dev) {
+        if (cudaMalloc((void**)&din, m * n * sizeof(double2)) != cudaSuccess) fail(DSBCG_ERR_OOM);
+        else cudaMemcpyAsync(din, in, m * n * sizeof(double2), cudaMemcpyHostToDevice, c->st);
+    }
+    if (rs == DSBCG_OK && !out_dev) {
+        if (cudaMalloc((void**)&dout, m * n * sizeof(double2)) != cudaSuccess) fail(DSBCG_ERR_OOM);
+    }
+    if (rs == DSBCG_OK) {
+        const double2* src = in_dev ? (const double2*)in : din;
+        double2* dst = out_dev ? (double2*)out : dout;
+        pack_any(c, storage, a, src, m);
+        if (op == DSBCG_OP_A) {
+            apply_op(c, storage, b, t, a, t2, ld, nullptr, m, m, c->hscale, c->st, DSBCG_KCLASS_DSLASH);
+        } else if (c->schur) {
+            apply_dhat(c, storage, b, a, t, ld, op == DSBCG_OP_DDAG, nullptr, m, m, c->hscale, c->st,
+                       DSBCG_KCLASS_DSLASH);
+        } else {
+            Prof p(c, DSBCG_KCLASS_DSLASH);
+            launch_dslash(storage, b, a, ld, c->links[storage], c->g, c->kappa, op == DSBCG_OP_DDAG, nullptr, m, m,
+                          c->hscale, c->st);
+        }
+        unpack_any(c, storage, dst, b, m);
+        if (!out_dev) cudaMemcpyAsync(out, dout, m * n * sizeof(double2), cudaMemcpyDeviceToHost, c->st);
+        if (cudaGetLastError() != cudaSuccess) fail(DSBCG_ERR_CUDA);
+        if (cudaStreamSynchronize(c->st) != cudaSuccess) fail(DSBCG_ERR_CUDA);
+        prof_collect(c);
+    }
+    cudaFree(a);
+    cudaFree(b);
+    cudaFree(t);
+    if (t2) cudaFree(t2);
+    if (din) cudaFree(din);
+    if (dout) cudaFree(dout);
+    return rs;
+}
+
+dsbcg_status dsbcg_set_operator(dsbcg_ctx* c, int op) {
+    if (!c || (op != DSBCG_OPERATOR_NORMAL && op != DSBCG_OPERATOR_SCHUR)) return DSBCG_ERR_ARG;
+    if (op == DSBCG_OPERATOR_SCHUR)
+        for (int d = 0; d < 4; ++d)
+            if (c->g.L[d] % 2) return DSBCG_ERR_ARG;
+    if ((op == DSBCG_OPERATOR_SCHUR) == (c->schur != 0)) return DSBCG_OK;
+    free_ws(c);                          // workspaces are sized for the field length
+    c->schur = op == DSBCG_OPERATOR_SCHUR;
+    c->Vf = c->schur ? c->V / 2 : c->V;
+    c->n = 12 * c->Vf;
+    c->ld = (c->n + 127) / 128 * 128;
+    c->hscale = (float)ldexp(1.0, (int)lround(0.5 * log2((double)c->n)));
+    return DSBCG_OK;
+}
+
 dsbcg_status dsbcg_force(dsbcg_ctx* c, int m, int s, const void* X, const void* Lambda, const double* weights,
                          int storage, void* dU) {
     if (!c || !X || !Lambda || !dU || m < 1 || s < 1 || (size_t)m * s > 4096) return DSBCG_ERR_ARG;
     if (!c->gauge_ok) return DSBCG_ERR_ARG;
     if (storage != P64 && storage != P32) return DSBCG_ERR_UNSUPPORTED;
+    if (c->schur) return DSBCG_ERR_UNSUPPORTED;     // the force of the normal operator only
     CKS(ensure_links(c, storage));
     const size_t n = c->n, ld = c->ld, V = c->V;
     const int nf = m * s;
@@ -1202,9 +1338,9 @@ dsbcg_status dsbcg_force(dsbcg_ctx* c, int m, int s, const void* X, const void* 
             ls = stage;
         }
         launch_pack_fields(storage, lf, ld, ls, nf, V, 1.f, c->st);
-        launch_dslash(storage, ex, xf, ld, c->links[storage], c->g, c->kappa, 0, 0, nullptr, nf, std::min(nf, 16), 1.f,
+        launch_dslash(storage, ex, xf, ld, c->links[storage], c->g, c->kappa, 0, nullptr, nf, std::min(nf, 16), 1.f,
                       c->st);
-        launch_dslash(storage, el, lf, ld, c->links[storage], c->g, c->kappa, 0, 0, nullptr, nf, std::min(nf, 16), 1.f,
+        launch_dslash(storage, el, lf, ld, c->links[storage], c->g, c->kappa, 0, nullptr, nf, std::min(nf, 16), 1.f,
                       c->st);
         {
             Prof p(c, DSBCG_KCLASS_OTHER);
@@ -1226,6 +1362,143 @@ dsbcg_status dsbcg_force(dsbcg_ctx* c, int m, int s, const void* X, const void* 
     cudaFree(wf);
     if (stage) cudaFree(stage);
     return rs;
+}
+
+dsbcg_status dsbcg_backward(dsbcg_ctx* c, int m, const void* B, int s, const double* sigma, const void* X,
+                            const void* G, const double* g_weights, double g_direct, double tol,
+                            const dsbcg_params* params, void* gB, double* gsigma, void* gU, void* Lambda,
+                            dsbcg_stats* stats) {
+    Range r_bwd("dsbcg_backward");
+    auto t0 = std::chrono::steady_clock::now();
+    if (!c || !G || !sigma || m < 1 || m > M_MAX || s < 1 || s > S_MAX) return DSBCG_ERR_ARG;
+    if (!X && !B) return DSBCG_ERR_ARG;
+    if (!c->gauge_ok) return DSBCG_ERR_ARG;
+    if (gU && c->schur) return DSBCG_ERR_UNSUPPORTED;
+    if (g_weights)
+        for (int j = 0; j < s; ++j)
+            if (!isfinite(g_weights[j])) return DSBCG_ERR_ARG;
+    if (!isfinite(g_direct) || (g_direct != 0.0 && !g_weights)) return DSBCG_ERR_ARG;
+    dsbcg_params prm;
+    if (params) prm = *params;
+    else dsbcg_params_default(&prm);
+    prm.x0 = 0;
+    const size_t n = c->n;
+    const size_t cnt = (size_t)m * n, blk = (size_t)s * cnt;
+    // X is needed by the shift gradient and the force only
+    const bool need_x = gsigma || gU;
+    std::vector<void*> owned;
+    auto dalloc = [&](void** p, size_t bytes) -> dsbcg_status {
+        if (cudaMalloc(p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return DSBCG_ERR_OOM;
+        }
+        owned.push_back(*p);
+        return DSBCG_OK;
+    };
+    dsbcg_status rs = DSBCG_OK, solve_st = DSBCG_OK;
+    int steps = 0, restarts = 0, deflations = 0, final_rank = 0;
+    long long mvms = 0;
+    auto add_stats = [&](const dsbcg_stats& q) {
+        steps += q.block_steps;
+        mvms += q.mvms;
+        deflations += q.deflations;
+        restarts += q.restarts;
+        final_rank = q.final_rank;
+    };
+    auto run = [&]() -> dsbcg_status {
+        double2* Xd = nullptr;
+        if (need_x) {
+            if (X && is_device_ptr(X)) {
+                Xd = (double2*)X;
+            } else {
+                CKS(dalloc((void**)&Xd, blk * sizeof(double2)));
+                if (X) {
+                    CK(cudaMemcpyAsync(Xd, X, blk * sizeof(double2), cudaMemcpyHostToDevice, c->st));
+                } else {
+                    // recompute the solutions instead of keeping them (memory)
+                    dsbcg_stats q{};
+                    const dsbcg_status st = solve_core(c, m, B, 1, s, sigma, tol, &prm, Xd, &q, nullptr);
+                    if (st < 0) return st;
+                    if (st == DSBCG_NOT_CONVERGED) solve_st = st;
+                    add_stats(q);
+                }
+            }
+        }
+        // adjoint solves (sigma_j I + A) Lambda_j = G_j (sigma_j I + A is hermitian)
+        double2* Ld = nullptr;
+        if (Lambda && is_device_ptr(Lambda)) Ld = (double2*)Lambda;
+        else CKS(dalloc((void**)&Ld, blk * sizeof(double2)));
+        {
+            dsbcg_stats q{};
+            q.true_relres = stats ? stats->true_relres : nullptr;
+            q.conv_step = stats ? stats->conv_step : nullptr;
+            // one block with per-shift weights: one joint DSBlockCG solve, then
+            // Lambda_j = w_j (sigma_j + A)^{-1} G; per-shift blocks: all shifts
+            // in one call, each on its own refinement lane
+            const dsbcg_status st = g_weights ? solve_core(c, m, G, 1, s, sigma, tol, &prm, Ld, &q, nullptr)
+                                              : solve_core(c, m, G, s, s, sigma, tol, &prm, Ld, &q, nullptr);
+            if (st < 0) return st;
+            if (st == DSBCG_NOT_CONVERGED) solve_st = st;
+            add_stats(q);
+        }
+        if (g_weights) {
+            Prof p(c, DSBCG_KCLASS_OTHER);
+            launch_scale_blocks(Ld, s, cnt, g_weights, c->st);
+        }
+        // dL/dB = g_direct G + sum_j Lambda_j
+        if (gB) {
+            const bool dev = is_device_ptr(gB);
+            double2* dst = (double2*)gB;
+            if (!dev) CKS(dalloc((void**)&dst, cnt * sizeof(double2)));
+            const double2* gdev = (const double2*)G;
+            if (g_direct != 0.0 && !is_device_ptr(G)) {
+                double2* t = nullptr;
+                CKS(dalloc((void**)&t, cnt * sizeof(double2)));
+                CK(cudaMemcpyAsync(t, G, cnt * sizeof(double2), cudaMemcpyHostToDevice, c->st));
+                gdev = t;
+            }
+            {
+                Prof p(c, DSBCG_KCLASS_OTHER);
+                launch_sum_blocks(dst, Ld, s, cnt, gdev, g_direct, c->st);
+            }
+            if (!dev) CK(cudaMemcpyAsync(gB, dst, cnt * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
+        }
+        // dL/dsigma_j = -Re tr(Lambda_j^H X_j)
+        if (gsigma) {
+            const int nblk = residual_blocks(cnt);
+            double* part = nullptr;
+            double* out = nullptr;
+            CKS(dalloc((void**)&part, (size_t)nblk * s * sizeof(double)));
+            CKS(dalloc((void**)&out, (size_t)s * sizeof(double)));
+            {
+                Prof p(c, DSBCG_KCLASS_OTHER, 2);
+                launch_dot_re_blocks(Ld, Xd, s, cnt, part, nblk, out, c->st);
+            }
+            std::vector<double> h(s);
+            CK(cudaMemcpyAsync(h.data(), out, s * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+            CK(cudaStreamSynchronize(c->st));
+            for (int j = 0; j < s; ++j) gsigma[j] = -h[j];
+        }
+        // dL/dU: the force kernel over (X_j, Lambda_j)
+        if (gU) CKS(dsbcg_force(c, m, s, Xd, Ld, nullptr, prm.storage == DSBCG_PREC_FP64 ? P64 : P32, gU));
+        if (Lambda && (void*)Ld != Lambda)
+            CK(cudaMemcpyAsync(Lambda, Ld, blk * sizeof(double2), cudaMemcpyDeviceToHost, c->st));
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(c->st));
+        return DSBCG_OK;
+    };
+    rs = run();
+    cudaStreamSynchronize(c->st);
+    for (void* p : owned) cudaFree(p);
+    if (stats) {
+        stats->block_steps = steps;
+        stats->mvms = mvms;
+        stats->deflations = deflations;
+        stats->restarts = restarts;
+        stats->final_rank = final_rank;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return rs != DSBCG_OK ? rs : solve_st;
 }
 
 }  // extern "C"
@@ -1267,7 +1540,7 @@ extern "C" dsbcg_status dsbcg_apply_static(dsbcg_ctx* c, int op, int storage, in
     if (!c || !in || !out || m < 1 || op < 0 || op > 2 || storage < 0 || storage > PDD) return DSBCG_ERR_ARG;
     if (!c->gauge_ok) return DSBCG_ERR_ARG;
     if (!is_device_ptr(in) || !is_device_ptr(out)) return DSBCG_ERR_ARG;
-    if (!c->links[storage]) return DSBCG_ERR_UNSUPPORTED;
+    if (!c->links[storage] || c->schur) return DSBCG_ERR_UNSUPPORTED;
     const size_t ld = hp_ld(c, storage);
     const size_t fb = prec_elem_bytes(storage) * c->ld;
     const size_t nbuf = op == DSBCG_OP_A ? 3 : 2;
@@ -1281,12 +1554,12 @@ extern "C" dsbcg_status dsbcg_apply_static(dsbcg_ctx* c, int op, int storage, in
     double2* dst = (double2*)out;
     pack_any(c, storage, a, src, m);
     if (op == DSBCG_OP_D) {
-        launch_dslash(storage, b, a, ld, c->links[storage], c->g, c->kappa, 0, 0, nullptr, m, m, c->hscale, c->st);
+        launch_dslash(storage, b, a, ld, c->links[storage], c->g, c->kappa, 0, nullptr, m, m, c->hscale, c->st);
     } else if (op == DSBCG_OP_DDAG) {
-        launch_dslash(storage, b, a, ld, c->links[storage], c->g, c->kappa, 1, 1, nullptr, m, m, c->hscale, c->st);
+        launch_dslash(storage, b, a, ld, c->links[storage], c->g, c->kappa, 1, nullptr, m, m, c->hscale, c->st);
     } else {
-        launch_dslash(storage, t, a, ld, c->links[storage], c->g, c->kappa, 0, 0, nullptr, m, m, c->hscale, c->st);
-        launch_dslash(storage, b, t, ld, c->links[storage], c->g, c->kappa, 1, 1, nullptr, m, m, c->hscale, c->st);
+        launch_dslash(storage, t, a, ld, c->links[storage], c->g, c->kappa, 0, nullptr, m, m, c->hscale, c->st);
+        launch_dslash(storage, b, t, ld, c->links[storage], c->g, c->kappa, 1, nullptr, m, m, c->hscale, c->st);
     }
     unpack_any(c, storage, dst, b, m);
     CK(cudaGetLastError());

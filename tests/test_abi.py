@@ -29,6 +29,7 @@ def test_host_only_calls(L):
     p = dsbcg.Params()
     L.dsbcg_params_default(ctypes.byref(p))
     assert p.storage == 1 and p.freeze_converged == 1 and p.max_restarts > 0
+    assert p.fp64_residuals == 1            # IEEE FP64 reliable updates by default
     for code in (0, 1, -1, -2, -3, -4, -5, -6):
         assert len(L.dsbcg_error_string(code)) > 0
     # argument validation happens before any device work
@@ -36,6 +37,9 @@ def test_host_only_calls(L):
     bad = (ctypes.c_int * 4)(4, 4, 1, 4)
     assert L.dsbcg_create(ctypes.byref(ctx), bad, ctypes.c_void_p(1), 0.1, 1, None) == -1
     assert L.dsbcg_solve(None, 1, None, 1, None, 1e-8, None, None, None) == -1
+    assert L.dsbcg_solve_rational(None, 1, None, 1, None, 0.0, None, 1e-8, None, None, None, None) == -1
+    assert L.dsbcg_backward(None, 1, None, 1, None, None, None, None, 0.0, 1e-8, None, None, None, None, None,
+                            None) == -1
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
