@@ -317,6 +317,17 @@ dsbcg_status dsbcg_apply_static(dsbcg_ctx* ctx, int op, int storage, int m, cons
 dsbcg_status dsbcg_force(dsbcg_ctx* ctx, int m, int s, const void* X, const void* Lambda,
                          const double* weights, int storage, void* dU);
 
+/* Test hook for the failure path of the device-side waits; not for
+ * production use.  Every shared-memory wait in the library's kernels is
+ * bounded: a kernel whose wait gives up drains its own bulk copies, records
+ * a timeout in the solve's control block and returns, and the call returns
+ * DSBCG_ERR_CUDA with the GPU still usable.  With polls >= 0, the first wait
+ * of every consumer warp of the staged block Gram kernel (the product
+ * V_k^H A V_k of each block step) gives up after `polls` non-blocking tests
+ * (0: at once), so a test can take that path without any fault.  polls < 0
+ * restores the normal limit (the default). */
+dsbcg_status dsbcg_debug_first_wait(dsbcg_ctx* ctx, int polls);
+
 /* Per-kernel CUDA-event timing inside dsbcg_solve (off by default). */
 dsbcg_status dsbcg_set_profiling(dsbcg_ctx* ctx, int on);
 

@@ -27,15 +27,16 @@ int gram_blocks(size_t n, int nf_max) {
 }
 
 void launch_gram(int prec, const void* X, const void* Y, size_t ld, size_t n, const Ctl* ctl, int nf_static,
-                 int nf_max, int herm, int diag_yy, double* partials, int nblk, float hscale, cudaStream_t st) {
+                 int nf_max, int herm, int diag_yy, double* partials, int nblk, float hscale, cudaStream_t st,
+                 int first_wait) {
     if (nf_max <= 16) {
         // shared-memory tiled kernel: one CTA per partial slot, nblk CTAs
         Ctl* c = const_cast<Ctl*>(ctl);
         switch (prec) {
-            case P64: launch_gram_tile_t<P64>(X, Y, ld, n, c, nf_static, nf_max, herm, diag_yy, partials, nblk, hscale, st); break;
-            case P32: launch_gram_tile_t<P32>(X, Y, ld, n, c, nf_static, nf_max, herm, diag_yy, partials, nblk, hscale, st); break;
-            case PBF16: launch_gram_tile_t<PBF16>(X, Y, ld, n, c, nf_static, nf_max, herm, diag_yy, partials, nblk, hscale, st); break;
-            case PF16: launch_gram_tile_t<PF16>(X, Y, ld, n, c, nf_static, nf_max, herm, diag_yy, partials, nblk, hscale, st); break;
+            case P64: launch_gram_tile_t<P64>(X, Y, ld, n, c, nf_static, nf_max, herm, diag_yy, partials, nblk, hscale, st, first_wait); break;
+            case P32: launch_gram_tile_t<P32>(X, Y, ld, n, c, nf_static, nf_max, herm, diag_yy, partials, nblk, hscale, st, first_wait); break;
+            case PBF16: launch_gram_tile_t<PBF16>(X, Y, ld, n, c, nf_static, nf_max, herm, diag_yy, partials, nblk, hscale, st, first_wait); break;
+            case PF16: launch_gram_tile_t<PF16>(X, Y, ld, n, c, nf_static, nf_max, herm, diag_yy, partials, nblk, hscale, st, first_wait); break;
         }
         return;
     }

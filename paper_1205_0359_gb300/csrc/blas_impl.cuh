@@ -303,10 +303,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return done != 0;
 }
+// one non-blocking test of the phase
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
 // bounded wait; returns false on timeout
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     for (long it = 0; it < MBAR_SPIN_LIMIT; ++it)
         if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+// bounded wait that also gives up as soon as *abort is set (by another warp
+// of the CTA whose own wait gave up)
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, const volatile int* abort) {
+    for (long it = 0; it < MBAR_SPIN_LIMIT; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort) return false;
+    }
     return false;
 }
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -352,7 +371,7 @@ __global__ void __launch_bounds__(544) gram_tile_kernel(const typename Tr<P>::S2
                                                         const typename Tr<P>::S2* __restrict__ Y, size_t ld,
                                                         size_t n, Ctl* __restrict__ ctl, int nf_static, int nf_max,
                                                         int herm, int diag_yy, double* __restrict__ partials,
-                                                        float hscale) {
+                                                        float hscale, int first_wait) {
     using C = typename Tr<P>::C;
     using R = typename Tr<P>::R;
     using SE = typename Tr<P>::S2;
@@ -374,12 +393,16 @@ __global__ void __launch_bounds__(544) gram_tile_kernel(const typename Tr<P>::S2
     const size_t ntr = (n + GR - 1) / GR;
     const size_t G = gridDim.x;
 
+    // set by a consumer warp whose wait gave up: the producer stops waiting
+    // for buffers that will not be released and drains its copies
+    __shared__ int aborted;
     if (threadIdx.x == 0) {
         for (int b = 0; b < GNST; ++b) {
             mbar_init(&full[b], 1);
             mbar_init(&empty[b], ncons);
         }
         mbar_fence_init();
+        aborted = 0;
     }
     __syncthreads();
     bool ok = true;
@@ -389,7 +412,7 @@ __global__ void __launch_bounds__(544) gram_tile_kernel(const typename Tr<P>::S2
             size_t it = 0;
             for (size_t q = blockIdx.x; q < ntr; q += G, ++it) {
                 const int b = (int)(it % GNST);
-                if (it >= GNST && !mbar_wait(&empty[b], (uint32_t)((it / GNST - 1) & 1))) {
+                if (it >= GNST && !mbar_wait_or_abort(&empty[b], (uint32_t)((it / GNST - 1) & 1), &aborted)) {
                     ok = false;
                     break;
                 }
@@ -428,8 +451,18 @@ __global__ void __launch_bounds__(544) gram_tile_kernel(const typename Tr<P>::S2
         size_t it = 0;
         for (size_t q = blockIdx.x; q < ntr; q += G, ++it) {
             const int b = (int)(it % GNST);
-            if (!mbar_wait(&full[b], (uint32_t)((it / GNST) & 1))) {
+            bool got;
+            if (it == 0 && first_wait >= 0) {
+                // test hook (first_wait >= 0): the first wait gives up after
+                // first_wait non-blocking tests, taking the timeout path below
+                got = false;
+                for (int k = 0; k < first_wait && !got; ++k) got = mbar_test(&full[b], 0u);
+            } else {
+                got = mbar_wait(&full[b], (uint32_t)((it / GNST) & 1));
+            }
+            if (!got) {
                 ok = false;
+                if (lane == 0) atomicExch(&aborted, 1);
                 break;
             }
             const int rows = (int)((n - q * GR) < (size_t)GR ? (n - q * GR) : (size_t)GR);
@@ -484,7 +517,7 @@ __global__ void __launch_bounds__(544) gram_tile_kernel(const typename Tr<P>::S2
     }
     if (__syncthreads_or(!ok)) {
         // a wait gave up: poison every partial of this CTA
-        if (threadIdx.x == 0 && ctl) atomicExch(&ctl->status, ST_WAIT_TIMEOUT);
+        if (threadIdx.x == 0 && ctl) atomicCAS(&ctl->status, 0, ST_WAIT_TIMEOUT);
         for (int t = threadIdx.x; t < ncons * GSLOTS; t += blockDim.x) {
             const size_t at = ((size_t)(t / GSLOTS) * G + blockIdx.x) * GSLOTS + t % GSLOTS;
             if constexpr (P == P64)
@@ -497,7 +530,8 @@ __global__ void __launch_bounds__(544) gram_tile_kernel(const typename Tr<P>::S2
 
 template <int P>
 void launch_gram_tile_t(const void* X, const void* Y, size_t ld, size_t n, Ctl* ctl, int nf_static, int nf_max,
-                        int herm, int diag_yy, double* partials, int nblk, float hscale, cudaStream_t st) {
+                        int herm, int diag_yy, double* partials, int nblk, float hscale, cudaStream_t st,
+                        int first_wait) {
     using SE = typename Tr<P>::S2;
     constexpr int GNST = gram_stages<P>();
     const int npb = ntiles_of(nf_max, herm);
@@ -506,7 +540,7 @@ void launch_gram_tile_t(const void* X, const void* Y, size_t ld, size_t n, Ctl* 
     static std::atomic<unsigned long long> devs{0};
     max_dyn_smem_once(gram_tile_kernel<P>, (int)(GNST * 2 * 16 * GR * sizeof(SE) + 2 * GNST * sizeof(uint64_t)), devs);
     gram_tile_kernel<P><<<nblk, (npb + 1) * 32, smem, st>>>((const SE*)X, (const SE*)Y, ld, n, ctl, nf_static, nf_max, herm,
-                                                      diag_yy, partials, hscale);
+                                                      diag_yy, partials, hscale, first_wait);
 }
 
 // V_{k+1} = W S (one thread per row; W and V in the storage precision)
@@ -623,7 +657,7 @@ __global__ void __launch_bounds__(ROWS / su_rpt(NF, PW)) shift_tile_kernel(
     if (!__syncthreads_and(ok)) {
         if (tid == 0) {
             mbar_wait(bar, 0);
-            atomicExch(&ctl->status, ST_WAIT_TIMEOUT);
+            atomicCAS(&ctl->status, 0, ST_WAIT_TIMEOUT);
         }
         return;
     }

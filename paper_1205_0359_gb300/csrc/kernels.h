@@ -32,6 +32,11 @@ void launch_unpack_pairs(double2* dst, const float2* src, size_t ld, int m, size
 void launch_accumulate_pairs(float2* y, size_t ld, const float2* x, size_t ldx, int m, size_t n, cudaStream_t st);
 void launch_residual_pairs(float2* r, const float2* b, const float2* x, const float2* ax, size_t ld, int m,
                            size_t n, double sigma, double* partials, int nblk, cudaStream_t st);
+// 12-real links of FP32 / 16-bit storage: rows 0, 1 of each link, [mu][e < 6][site]
+void launch_pack_links12(int prec, void* dst, const double2* src, size_t V, cudaStream_t st);
+// *flag |= 1 unless every link of the canonical field (nlinks 3x3 matrices)
+// is in SU(3) to tol (orthonormal rows 0, 1; row 2 = conj(row 0 x row 1))
+void launch_check_su3(const double2* src, size_t nlinks, double tol, int* flag, cudaStream_t st);
 // counts NaN/Inf entries of a complex128 array into *flag (device int)
 void launch_check_finite(const double2* p, size_t count, int* flag, cudaStream_t st);
 // y_f += x_f (FP64 += work precision), fields listed by index arrays on the host
@@ -60,9 +65,12 @@ void launch_dot_re_blocks(const double2* a, const double2* b, int s, size_t cnt,
 // ---- dslash.cu ------------------------------------------------------------
 // out_f = D in_f (dag = 0) or D^H in_f = gamma_5 D gamma_5 in_f (dag = 1)
 // for fields f < nf, where nf = ctl->mk when ctl != NULL, else nf_static.
+// links12 (FP32 / 16-bit only, may be NULL): the same links in the 12-real
+// layout of launch_pack_links12, used instead of `links` when given
 void launch_dslash(int prec, void* out, const void* in, size_t ld, const void* links,
                    const Geom& g, double kappa, int dag, const Ctl* ctl,
-                   int nf_static, int nf_max, float hscale, cudaStream_t st);
+                   int nf_static, int nf_max, float hscale, cudaStream_t st,
+                   const void* links12 = nullptr);
 
 // Half-lattice hopping term of the even-odd operator (every extent even; half
 // fields of V / 2 sites, half index = canonical site / 2):
@@ -77,9 +85,13 @@ void launch_dslash_half(int prec, void* out, const void* in, const void* src, si
 int gram_blocks(size_t n, int nf_max);
 // partial sums of X^H Y (nf x nf, FP64) per CTA; herm = 1 computes only the
 // upper triangle of tiles (X == Y); diag_yy = 1 also sums |y_j|^2.
+// first_wait >= 0 (a test hook; default -1 = off): the first shared-memory
+// wait of each consumer warp of the staged kernel (nf_max <= 16) gives up
+// after first_wait non-blocking tests and the kernel takes its timeout path
+// (copies drained, ST_WAIT_TIMEOUT in ctl->status, NaN partials)
 void launch_gram(int prec, const void* X, const void* Y, size_t ld, size_t n, const Ctl* ctl,
                  int nf_static, int nf_max, int herm, int diag_yy, double* partials, int nblk,
-                 float hscale, cudaStream_t st);
+                 float hscale, cudaStream_t st, int first_wait = -1);
 size_t gram_partial_doubles(int nf_max);
 // reduce partials -> G (FP64, M_MAX x M_MAX, complex), diag (M_MAX)
 void launch_gram_reduce(const double* partials, int nblk, int nf_max, int herm, int diag_yy,

@@ -58,6 +58,60 @@ __global__ void pack_links_kernel(typename Tr<P>::S2* __restrict__ dst, const do
     }
 }
 
+// 12-real links: rows 0 and 1 of every SU(3) link, [mu][entry e < 6][site]
+// (row 2 = conj(row 0 x row 1) is rebuilt by the stencil)
+template <int P>
+__global__ void pack_links12_kernel(typename Tr<P>::S2* __restrict__ dst, const double2* __restrict__ src, size_t V) {
+    const size_t total = V * 24;
+    using R = typename Tr<P>::R;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const size_t x = t / 24;
+        const int r = (int)(t % 24);
+        const int mu = r / 6, e = r % 6;
+        const double2 v = src[x * 36 + mu * 9 + e];
+        Elem<P>::st(dst, ((size_t)mu * 6 + e) * V + x, mk(R(v.x), R(v.y)), R(1));
+    }
+}
+
+// *flag = 1 if some link is not in SU(3) to tol: rows 0 and 1 orthonormal and
+// row 2 = conj(row 0 x row 1), each entry to tol (FP64)
+__global__ void check_su3_kernel(const double2* __restrict__ src, size_t nlinks, double tol, int* flag) {
+    int bad = 0;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < nlinks;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const double2* u = src + t * 9;
+        double2 r[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) r[e] = u[e];
+        // <r_i, r_j> - delta_ij for i, j in {0, 1}
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = i; j < 2; ++j) {
+                double re = 0.0, im = 0.0;
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    const double2 a = r[i * 3 + b], c = r[j * 3 + b];
+                    re += a.x * c.x + a.y * c.y;            // conj(a) c
+                    im += a.x * c.y - a.y * c.x;
+                }
+                if (i == j) re -= 1.0;
+                if (!(fabs(re) <= tol && fabs(im) <= tol)) bad = 1;
+            }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int i = (k + 1) % 3, j = (k + 2) % 3;
+            // conj(r0_i r1_j - r0_j r1_i)
+            const double2 a = r[i], b = r[3 + j], c = r[j], d = r[3 + i];
+            const double x = (a.x * b.x - a.y * b.y) - (c.x * d.x - c.y * d.y);
+            const double y = -((a.x * b.y + a.y * b.x) - (c.x * d.y + c.y * d.x));
+            if (!(fabs(x - r[6 + k].x) <= tol && fabs(y - r[6 + k].y) <= tol)) bad = 1;
+        }
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
 __global__ void check_finite_kernel(const double2* __restrict__ p, size_t count, int* flag) {
     int bad = 0;
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count;
@@ -366,6 +420,19 @@ void launch_pack_links(int prec, void* dst, const double2* src, size_t V, cudaSt
         case PBF16: pack_links_kernel<PBF16><<<g, 256, 0, st>>>((__nv_bfloat162*)dst, src, V); break;
         case PF16: pack_links_kernel<PF16><<<g, 256, 0, st>>>((__half2*)dst, src, V); break;
     }
+}
+
+void launch_pack_links12(int prec, void* dst, const double2* src, size_t V, cudaStream_t st) {
+    const int g = grid_for(V * 24);
+    switch (prec) {
+        case P32: pack_links12_kernel<P32><<<g, 256, 0, st>>>((float2*)dst, src, V); break;
+        case PBF16: pack_links12_kernel<PBF16><<<g, 256, 0, st>>>((__nv_bfloat162*)dst, src, V); break;
+        case PF16: pack_links12_kernel<PF16><<<g, 256, 0, st>>>((__half2*)dst, src, V); break;
+    }
+}
+
+void launch_check_su3(const double2* src, size_t nlinks, double tol, int* flag, cudaStream_t st) {
+    check_su3_kernel<<<grid_for(nlinks), 256, 0, st>>>(src, nlinks, tol, flag);
 }
 
 void launch_check_finite(const double2* p, size_t count, int* flag, cudaStream_t st) {

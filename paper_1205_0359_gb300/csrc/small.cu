@@ -633,7 +633,7 @@ __global__ void small_step_kernel(SmallStateT<T>* ss, Ctl* ctl, const double* __
     bsync();
     if (!gj_inverse<T>(Dl, MM, mk_, col)) {
         if (threadIdx.x == 0) {
-            atomicExch(&ctl->status, ST_NOT_HPD);
+            atomicCAS(&ctl->status, 0, ST_NOT_HPD);
             active[j] = 0;
             sf.alive = 0;
         }

@@ -97,8 +97,13 @@ struct dsbcg_ctx {
     cudaStream_t st = nullptr;
     double2* gauge64 = nullptr;          // canonical copy of the links (device)
     void* links[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // per Prec (PDD: double-float)
+    // 12-real copies (rows 0, 1) for FP32 / 16-bit storage, packed when every
+    // link of the field is in SU(3) to 1e-10 (su3); the stencil rebuilds row 2
+    void* links12[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool su3 = false;
     float hscale = 1.f;
     bool gauge_ok = false;               // gauge64 holds a checked field and links[] were packed from it
+    int debug_first_wait = -1;           // test hook of the block Gram kernel (dsbcg_debug_first_wait)
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<KEvent> ev_live;
@@ -232,6 +237,13 @@ dsbcg_status ensure_links(dsbcg_ctx* c, int prec) {
     launch_pack_links(prec, p, c->gauge64, c->V, c->st);
     CK(cudaGetLastError());
     c->links[prec] = p;
+    if (c->su3 && (prec == P32 || prec == PBF16 || prec == PF16) && !c->links12[prec]) {
+        void* q = nullptr;
+        CK(cudaMalloc(&q, c->V * 24 * prec_elem_bytes(prec)));
+        launch_pack_links12(prec, q, c->gauge64, c->V, c->st);
+        CK(cudaGetLastError());
+        c->links12[prec] = q;
+    }
     return DSBCG_OK;
 }
 
@@ -493,11 +505,11 @@ void apply_op(dsbcg_ctx* c, int p, void* out, void* mid, const void* in, void* t
     }
     {
         Prof q(c, cls, 1, st);
-        launch_dslash(p, mid, in, ld, c->links[p], c->g, c->kappa, 0, ctl, nf_static, nf_max, hs, st);
+        launch_dslash(p, mid, in, ld, c->links[p], c->g, c->kappa, 0, ctl, nf_static, nf_max, hs, st, c->links12[p]);
     }
     {
         Prof q(c, cls, 1, st);
-        launch_dslash(p, out, mid, ld, c->links[p], c->g, c->kappa, 1, ctl, nf_static, nf_max, hs, st);
+        launch_dslash(p, out, mid, ld, c->links[p], c->g, c->kappa, 1, ctl, nf_static, nf_max, hs, st, c->links12[p]);
     }
 }
 
@@ -610,7 +622,8 @@ dsbcg_status lane_enqueue(dsbcg_ctx* c, Lane& L) {
         apply_op(c, prec, L.y, L.zw, Vk, L.eotmp, ld, L.ctl, 0, m_in, c->hscale, st, DSBCG_KCLASS_DSLASH);
         {
             Prof p(c, DSBCG_KCLASS_GRAM, 1, st);
-            launch_gram(prec, Vk, L.y, ld, n, L.ctl, 0, m_in, 0, 1, L.partials, L.nblk, c->hscale, st);
+            launch_gram(prec, Vk, L.y, ld, n, L.ctl, 0, m_in, 0, 1, L.partials, L.nblk, c->hscale, st,
+                        c->debug_first_wait);
         }
         {
             Prof p(c, DSBCG_KCLASS_SMALL, 1, st);
@@ -1158,10 +1171,15 @@ dsbcg_status dsbcg_update_gauge(dsbcg_ctx* c, const void* gauge) {
     // holds no usable field: the old packed links go first, so that no
     // precision keeps links of the old field while gauge64 holds the new one.
     c->gauge_ok = false;
+    c->su3 = false;
     for (int p = 0; p < 5; ++p) {
         if (c->links[p]) {
             cudaFree(c->links[p]);
             c->links[p] = nullptr;
+        }
+        if (c->links12[p]) {
+            cudaFree(c->links12[p]);
+            c->links12[p] = nullptr;
         }
     }
     const size_t bytes = c->V * 36 * sizeof(double2);
@@ -1169,15 +1187,21 @@ dsbcg_status dsbcg_update_gauge(dsbcg_ctx* c, const void* gauge) {
     CK(cudaMemcpyAsync(c->gauge64, gauge, bytes, is_device_ptr(gauge) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                        c->st));
     int* flag = nullptr;
-    CK(cudaMalloc((void**)&flag, sizeof(int)));
+    CK(cudaMalloc((void**)&flag, 2 * sizeof(int)));
     cudaMemsetAsync(flag, 0, sizeof(int), c->st);
     launch_check_finite(c->gauge64, c->V * 36, flag, c->st);
     int h = 0;
     cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+    // a field in SU(3) to 1e-10 gets 12-real links for the reduced storages
+    int hs = 1;
+    cudaMemsetAsync(flag + 1, 0, sizeof(int), c->st);
+    launch_check_su3(c->gauge64, c->V * 4, 1e-10, flag + 1, c->st);
+    cudaMemcpyAsync(&hs, flag + 1, sizeof(int), cudaMemcpyDeviceToHost, c->st);
     const cudaError_t e = cudaStreamSynchronize(c->st);
     cudaFree(flag);
     CK(e);
     if (h) return DSBCG_ERR_NONFINITE;
+    c->su3 = (hs == 0);
     CKS(ensure_links(c, P64));
     c->gauge_ok = true;
     return DSBCG_OK;
@@ -1200,8 +1224,10 @@ dsbcg_status dsbcg_solve_rational(dsbcg_ctx* c, int m, const void* B, int s, con
 void dsbcg_destroy(dsbcg_ctx* c) {
     if (!c) return;
     free_ws(c);
-    for (int p = 0; p < 5; ++p)
+    for (int p = 0; p < 5; ++p) {
         if (c->links[p]) cudaFree(c->links[p]);
+        if (c->links12[p]) cudaFree(c->links12[p]);
+    }
     if (c->gauge64) cudaFree(c->gauge64);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     for (auto& k : c->ev_live) {
@@ -1209,6 +1235,12 @@ void dsbcg_destroy(dsbcg_ctx* c) {
         cudaEventDestroy(k.b);
     }
     delete c;
+}
+
+dsbcg_status dsbcg_debug_first_wait(dsbcg_ctx* c, int polls) {
+    if (!c) return DSBCG_ERR_ARG;
+    c->debug_first_wait = polls < 0 ? -1 : polls;
+    return DSBCG_OK;
 }
 
 dsbcg_status dsbcg_set_profiling(dsbcg_ctx* c, int on) {
@@ -1266,7 +1298,7 @@ dsbcg_status dsbcg_apply(dsbcg_ctx* c, int op, int storage, int m, const void* i
         } else {
             Prof p(c, DSBCG_KCLASS_DSLASH);
             launch_dslash(storage, b, a, ld, c->links[storage], c->g, c->kappa, op == DSBCG_OP_DDAG, nullptr, m, m,
-                          c->hscale, c->st);
+                          c->hscale, c->st, c->links12[storage]);
         }
         unpack_any(c, storage, dst, b, m);
         if (!out_dev) cudaMemcpyAsync(out, dout, m * n * sizeof(double2), cudaMemcpyDeviceToHost, c->st);
@@ -1339,9 +1371,9 @@ dsbcg_status dsbcg_force(dsbcg_ctx* c, int m, int s, const void* X, const void* 
         }
         launch_pack_fields(storage, lf, ld, ls, nf, V, 1.f, c->st);
         launch_dslash(storage, ex, xf, ld, c->links[storage], c->g, c->kappa, 0, nullptr, nf, std::min(nf, 16), 1.f,
-                      c->st);
+                      c->st, c->links12[storage]);
         launch_dslash(storage, el, lf, ld, c->links[storage], c->g, c->kappa, 0, nullptr, nf, std::min(nf, 16), 1.f,
-                      c->st);
+                      c->st, c->links12[storage]);
         {
             Prof p(c, DSBCG_KCLASS_OTHER);
             launch_force(storage, du, ex, lf, el, xf, ld, nf, wf, c->g, c->kappa, c->st);

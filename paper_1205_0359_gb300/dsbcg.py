@@ -93,6 +93,8 @@ def lib():
     L.dsbcg_backward.argtypes = [vp, ip, vp, ip, dpp, vp, vp, dpp, dp, dp, ctypes.POINTER(Params), vp, dpp, vp,
                                  vp, ctypes.POINTER(Stats)]
     L.dsbcg_backward.restype = ip
+    L.dsbcg_debug_first_wait.argtypes = [vp, ip]
+    L.dsbcg_debug_first_wait.restype = ip
     L.dsbcg_set_operator.argtypes = [vp, ip]
     L.dsbcg_set_operator.restype = ip
     L.dsbcg_set_profiling.argtypes = [vp, ip]
@@ -174,6 +176,12 @@ class Context:
 
     def update_gauge(self, U):
         _check(lib().dsbcg_update_gauge(self._ctx, _ptr(_as_c128(U))), "dsbcg_update_gauge")
+
+    def debug_first_wait(self, polls):
+        """dsbcg_debug_first_wait (test hook): polls >= 0 makes the block
+        Gram kernel's first wait give up after that many tests; -1 restores
+        the normal limit."""
+        _check(lib().dsbcg_debug_first_wait(self._ctx, int(polls)), "dsbcg_debug_first_wait")
 
     def set_profiling(self, on=True):
         _check(lib().dsbcg_set_profiling(self._ctx, int(bool(on))), "dsbcg_set_profiling")

@@ -76,3 +76,30 @@ def test_host_buffers_and_periodic_time():
     want = W.to_vector(out)
     assert np.max(np.abs(got - want)) < 1e-13 * np.max(np.abs(want))
     ctx.close()
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16", "bf16"])
+def test_links_off_su3_use_full_storage(storage):
+    """FP32 and 16-bit storages keep only rows 0 and 1 of each link when the
+    gauge field is in SU(3) (row 2 = conj(row 0 x row 1) is rebuilt); a field
+    off SU(3) by 1e-3 must fall back to all 9 entries and still match the
+    oracle to the storage tolerance.  The same field projected back onto
+    SU(3) then takes the 12-real path (also matched), and an update of the
+    gauge field switches between the two."""
+    dims = (4, 4, 4, 6)
+    U, F, kappa = _setup(dims, 6, 23)
+    rng = np.random.Generator(np.random.PCG64(24))
+    Ubad = U + 1e-3 * (rng.standard_normal(U.shape) + 1j * rng.standard_normal(U.shape))
+    dev = torch.device("cuda")
+    Ft = torch.from_numpy(F).to(dev)
+    ctx = dsbcg.Context(dims, torch.from_numpy(Ubad).to(dev), kappa)
+    try:
+        for Ucur in (Ubad, U, Ubad):
+            ctx.update_gauge(torch.from_numpy(Ucur).to(dev))
+            for op, ref in [("D", W.D_vec), ("A", W.A_vec)]:
+                got = ctx.apply(op, Ft, storage=storage).cpu().numpy()
+                want = ref(Ucur, kappa, dims, F)
+                err = np.linalg.norm(got - want, axis=1) / np.linalg.norm(want, axis=1)
+                assert err.max() < TOL[storage], (op, storage, err.max())
+    finally:
+        ctx.close()
