@@ -406,9 +406,12 @@ def run_ours(args):
 
     if rank == 0 and not args.no_compare:
         leg("comparison", lambda: run_comparison(dev, stream))
+        leg("comparison_near_critical", lambda: run_comparison(dev, stream, name="cmp_critical_16x16x16x16"))
     clk_mhz = (clk or {}).get("sm_mhz") or 2070.0
     if rank == 0 and not args.no_w3:
         leg("w3_precision_ladder", lambda: run_w3_ladder(dev, stream, peak, clk_mhz))
+    if rank == 0 and not args.no_schur:
+        leg("schur_operator", lambda: run_schur(dev, stream, wl, value / world, stats[-1]))
     if rank == 0 and args.sweeps:
         line["sweeps"] = run_sweeps(dev, stream)
 
@@ -471,7 +474,7 @@ def run_ours(args):
     del X, Xmix, B
     torch.cuda.empty_cache()
     # the 32^3 x 64 workload needs most of the device: run it alone
-    if rank == 0 and args.w5:
+    if rank == 0 and not args.no_w5:
         leg("w5_full_size", lambda: run_w5(dev, stream, peak, clk_mhz, fp64=not args.no_fp64))
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -608,6 +611,36 @@ def run_w3_ladder(dev, stream, peak, clk_mhz):
     return out
 
 
+def run_schur(dev, stream, wl, full_value, full_stats):
+    """The even-odd preconditioned operator on the headline lattice: the
+    same shifts and tolerance for sigma_j + Ahat on the odd sites, with the
+    odd-site half of the headline right-hand sides (FP32 storage, FP64
+    reliable updates, one timed solve after a one-step warm-up).  Ahat is a
+    different operator from A, so this compares cost, not solutions."""
+    import torch
+    from paper_1205_0359_gb300 import dsbcg
+    Lx, Ly, Lz, Lt = wl["dims"]
+    t, z, y, x = np.meshgrid(np.arange(Lt), np.arange(Lz), np.arange(Ly), np.arange(Lx), indexing="ij")
+    odd = np.nonzero(((x + y + z + t) % 2).reshape(-1) == 1)[0]
+    m, s = wl["B"].shape[0], len(wl["sigma"])
+    Bh = np.ascontiguousarray(wl["B"].reshape(m, -1, 12)[:, odd, :].reshape(m, -1))
+    ctx = dsbcg.Context(wl["dims"], torch.from_numpy(wl["U"]).to(dev), wl["kappa"], stream=stream)
+    ctx.set_operator("schur")
+    B = torch.from_numpy(Bh).to(dev)
+    X = torch.empty((s, m, B.shape[1]), dtype=torch.complex128, device=dev)
+    st, ms = _timed_solve(ctx, B, wl["sigma"], wl["tol"], "fp32", X, dev, stream)
+    ctx.close()
+    del X, B
+    value = m * s / (ms / 1e3)
+    return {"workload": "the headline lattice, shifts and tol; sigma_j + Dhat^H Dhat on the odd sites, "
+                        "Dhat = 1 - kappa^2 H_oe H_eo, odd-site half of the headline right-hand sides",
+            "systems_per_s": round(value, 3), "ms_per_solve": round(ms, 1), "block_steps": st["block_steps"],
+            "restarts": st["restarts"], "max_true_relres": float(st["true_relres"].max()), "valid": st["code"] == 0,
+            "full_operator": {"systems_per_s": round(full_value, 3), "block_steps": full_stats["block_steps"],
+                              "restarts": full_stats["restarts"]},
+            "schur_over_full": round(value / full_value, 3)}
+
+
 def run_w5(dev, stream, peak, clk_mhz, fp64=True):
     """32^3 x 64, m = 16 (b_16 = b_1 + 1e-9 noise), s = 8 shifts 1e-5..1,
     tol 1e-8 (~140 GB of HBM in FP32 storage): mixed precision (FP32 storage,
@@ -740,7 +773,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-df32", action="store_true", help="skip the double-float reliable-update form")
     ap.add_argument("--no-w3", action="store_true", help="skip the 24^3 x 48 storage-precision ladder")
-    ap.add_argument("--w5", action="store_true", help="also run the 32^3 x 64 workload (mixed and plain FP64)")
+    ap.add_argument("--no-w5", action="store_true", help="skip the 32^3 x 64 workload (mixed and plain FP64)")
+    ap.add_argument("--no-schur", action="store_true", help="skip the even-odd (Schur) operator leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-force", action="store_true", help="skip the gauge-force timing")
     ap.add_argument("--sweeps", action="store_true",

@@ -513,7 +513,9 @@ __global__ void small_init_kernel(SmallStateT<T>* ss, Ctl* ctl, const double2* _
     }
 }
 
-// alpha_k from the Gram partials of V_k^H Y, hermitised; coef_a = alpha and
+// alpha_k from the Gram partials of the upper tiles of V_k^H Y (alpha_k =
+// V_k^H A V_k is hermitian; the lower tiles are the conjugates of the upper
+// ones, the diagonal tiles are hermitised); coef_a = alpha and
 // coef_bh = beta_k^H in the work precision (M_MAX tiles); ||y_i||^2
 template <class T>
 __global__ void small_alpha_kernel(SmallStateT<T>* ss, const Ctl* __restrict__ ctl, const double* __restrict__ part,
@@ -523,7 +525,7 @@ __global__ void small_alpha_kernel(SmallStateT<T>* ss, const Ctl* __restrict__ c
     if (ctl->done) return;
     __shared__ T A[M_MAX * M_MAX];
     __shared__ R yy[M_MAX];
-    reduce_partials<T>(part, nblk, nf_max, 0, A, M_MAX, yy, wprec == P64);
+    reduce_partials<T>(part, nblk, nf_max, 1, A, M_MAX, yy, wprec == P64);
     __syncthreads();
     const int mk_ = ctl->mk, mp = ctl->k > 1 ? ctl->mprev : 0;
     const R half = S::r(0.5);

@@ -622,7 +622,9 @@ dsbcg_status lane_enqueue(dsbcg_ctx* c, Lane& L) {
         apply_op(c, prec, L.y, L.zw, Vk, L.eotmp, ld, L.ctl, 0, m_in, c->hscale, st, DSBCG_KCLASS_DSLASH);
         {
             Prof p(c, DSBCG_KCLASS_GRAM, 1, st);
-            launch_gram(prec, Vk, L.y, ld, n, L.ctl, 0, m_in, 0, 1, L.partials, L.nblk, c->hscale, st,
+            // alpha_k = V_k^H A V_k is hermitian: the upper 4 x 4 tiles of
+            // V_k^H Y only (their conjugates fill the lower ones)
+            launch_gram(prec, Vk, L.y, ld, n, L.ctl, 0, m_in, 1, 1, L.partials, L.nblk, c->hscale, st,
                         c->debug_first_wait);
         }
         {

@@ -140,6 +140,11 @@ WORKLOADS = {
         "cmp_16x16x16x16", (16, 16, 16, 16), 0.125, 0.5, 4, 7, "gaussian",
         tuple(log_shifts(1e-6, 1e-1, 7)), 1e-8, seed=12050359_6,
         note="the paper's algorithm comparison (Sec. 4, Table 1): 16^4, 4 RHS, 7 shifts over 1e-6..1e-1"),
+    "cmp_critical_16x16x16x16": Workload(
+        "cmp_critical_16x16x16x16", (16, 16, 16, 16), 0.15, 0.5, 4, 7, "gaussian",
+        tuple(log_shifts(1e-6, 1e-1, 7)), 1e-8, seed=12050359_7,
+        note="the comparison of Sec. 4 on a lattice near its critical kappa (smooth links, kappa 0.15), "
+             "where DSBlockCG needs fewer A applications than shifted CG"),
     "w5_32x32x32x64": Workload(
         "w5_32x32x32x64", (32, 32, 32, 64), 0.13, 0.6, 16, 8, "gaussian",
         tuple(log_shifts(1e-5, 1.0, 8)), 1e-8, seed=12050359_5, dependent="near",
