@@ -42,6 +42,9 @@ void launch_check_finite(const double2* p, size_t count, int* flag, cudaStream_t
 // y_f += x_f (FP64 += work precision), fields listed by index arrays on the host
 void launch_accumulate(int prec_x, double2* y, size_t ldy, const void* x, size_t ldx,
                        int m, size_t n, cudaStream_t st);
+// FP64 internal fields -> FP32 internal fields (same element order), m fields of n
+void launch_convert_64_32(float2* dst, size_t ldd, const double2* src, size_t lds, int m, size_t n,
+                          cudaStream_t st);
 // r_f = b_f - sigma * x_f - ax_f (all FP64), and per-field squared norms (partials)
 void launch_residual(double2* r, const double2* b, const double2* x, const double2* ax,
                      size_t ld, int m, size_t n, double sigma, double* norm2_partials,

@@ -201,6 +201,18 @@ __global__ void accumulate_pairs_kernel(float2* __restrict__ y, size_t ld, const
     }
 }
 
+// FP64 internal fields -> FP32 internal fields (same element order)
+__global__ void convert_64_32_kernel(float2* __restrict__ dst, size_t ldd, const double2* __restrict__ src,
+                                     size_t lds, int m, size_t n) {
+    const size_t total = (size_t)m * n;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const size_t f = t / n, i = t % n;
+        const double2 v = src[f * lds + i];
+        dst[f * ldd + i] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
+    }
+}
+
 constexpr int RES_THREADS = 256;
 
 // r = b - sigma x - ax for double-float fields (grid (nblk, m)); squared
@@ -446,6 +458,11 @@ void launch_accumulate(int prec_x, double2* y, size_t ldy, const void* x, size_t
         accumulate_kernel<P64><<<g, 256, 0, st>>>(y, ldy, (const double2*)x, ldx, m, n);
     else
         accumulate_kernel<P32><<<g, 256, 0, st>>>(y, ldy, (const float2*)x, ldx, m, n);
+}
+
+void launch_convert_64_32(float2* dst, size_t ldd, const double2* src, size_t lds, int m, size_t n,
+                          cudaStream_t st) {
+    convert_64_32_kernel<<<grid_for((size_t)m * n), 256, 0, st>>>(dst, ldd, src, lds, m, n);
 }
 
 int residual_blocks(size_t n) {

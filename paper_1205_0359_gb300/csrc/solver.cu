@@ -30,7 +30,9 @@
 #include <algorithm>
 #include <chrono>
 #include <deque>
+#include <functional>
 #include <mutex>
+#include <thread>
 #include <vector>
 
 #include "../../include/dsbcg.h"
@@ -79,6 +81,7 @@ struct Lane {
     double *res = nullptr, *sigma = nullptr, *target = nullptr;
     dsbcg::Ctl* h_ctl = nullptr;                  // pinned
     int* h_conv = nullptr;                        // pinned
+    int* h_active = nullptr;                      // pinned (joint lane): shifts updated in the last step
     // the inner solve in progress
     int m_in = 0, s_in = 0, prec = 0, step = 0, max_steps = 0, freeze = 0, poll_every = 1;
     int sfp64 = 1;                                // m x m scalar: FP64 (1) or double-float (0)
@@ -103,6 +106,10 @@ struct dsbcg_ctx {
     bool su3 = false;
     float hscale = 1.f;
     bool gauge_ok = false;               // gauge64 holds a checked field and links[] were packed from it
+    // refinement stream (true residuals, restarts' bookkeeping) beside the
+    // context's stream, and the events that order the two; created on first use
+    cudaStream_t rst = nullptr;
+    cudaEvent_t ev_joint = nullptr, ev_ref = nullptr;
     int debug_first_wait = -1;           // test hook of the block Gram kernel (dsbcg_debug_first_wait)
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -135,6 +142,7 @@ struct dsbcg_ctx {
         Ctl* h_ctl = nullptr;            // pinned
         double* h_norms = nullptr;       // pinned
         int* h_conv = nullptr;           // pinned
+        int* h_active = nullptr;         // pinned
         int nblk = 0, rblk = 0;
         std::vector<void*> mem;
         std::vector<Lane> lanes;        // [0]: the joint solve's buffers; then refinement lanes
@@ -225,6 +233,7 @@ void free_ws(dsbcg_ctx* c) {
     if (c->ws.h_ctl) cudaFreeHost(c->ws.h_ctl);
     if (c->ws.h_norms) cudaFreeHost(c->ws.h_norms);
     if (c->ws.h_conv) cudaFreeHost(c->ws.h_conv);
+    if (c->ws.h_active) cudaFreeHost(c->ws.h_active);
     c->ws = dsbcg_ctx::WS();
 }
 
@@ -300,6 +309,7 @@ dsbcg_status ensure_ws(dsbcg_ctx* c, int m, int s, int prec, int nbb) {
     CK(cudaMallocHost((void**)&w.h_ctl, sizeof(Ctl)));
     CK(cudaMallocHost((void**)&w.h_norms, (size_t)(s + 1) * m * sizeof(double)));
     CK(cudaMallocHost((void**)&w.h_conv, (size_t)s * m * sizeof(int)));
+    CK(cudaMallocHost((void**)&w.h_active, (size_t)s * sizeof(int)));
     w.m = m;
     w.s = s;
     w.prec = prec;
@@ -331,6 +341,7 @@ dsbcg_status ensure_ws(dsbcg_ctx* c, int m, int s, int prec, int nbb) {
     L0.target = w.target;
     L0.h_ctl = w.h_ctl;
     L0.h_conv = w.h_conv;
+    L0.h_active = w.h_active;
     w.lanes.assign(1, L0);
     return DSBCG_OK;
 }
@@ -517,32 +528,42 @@ void apply_op(dsbcg_ctx* c, int p, void* out, void* mid, const void* in, void* t
 // reads every link once
 inline double link_passes(const dsbcg_ctx* c) { return c->schur ? 4.0 : 2.0; }
 
-// out = A in (or Ahat in) for nf high-precision fields (tmp receives D in)
-void apply_Ahp(dsbcg_ctx* c, int hp, void* out, const void* in, void* tmp, int nf) {
-    apply_op(c, hp, out, tmp, in, c->ws.T64c, hp_ld(c, hp), nullptr, nf, nf, 1.f, c->st, DSBCG_KCLASS_RESIDUAL);
+// out = A in (or Ahat in) for nf high-precision fields (tmp receives D in), on stream st
+void apply_Ahp(dsbcg_ctx* c, int hp, void* out, const void* in, void* tmp, int nf, cudaStream_t st) {
+    apply_op(c, hp, out, tmp, in, c->ws.T64c, hp_ld(c, hp), nullptr, nf, nf, 1.f, st, DSBCG_KCLASS_RESIDUAL);
 }
 
-// r = b - sigma x - A x for m high-precision fields; squared column norms
-// into h_out (host)
+// r = b - sigma x - A x for m high-precision fields on stream st; squared
+// column norms into h_out (host).  While the stream works, `idle` (if given)
+// is called repeatedly (the solve keeps its lanes supplied meanwhile).
 dsbcg_status true_residual(dsbcg_ctx* c, int hp, double2* r, const double2* b, const double2* x, int m,
-                           double sigma, double* h_out) {
+                           double sigma, double* h_out, const std::function<dsbcg_status()>* idle, cudaStream_t st) {
     Range r_res("true residual");
     auto& w = c->ws;
-    apply_Ahp(c, hp, w.T64b, x, w.T64a, m);
+    apply_Ahp(c, hp, w.T64b, x, w.T64a, m, st);
     {
-        Prof p(c, DSBCG_KCLASS_RESIDUAL, 2);
+        Prof p(c, DSBCG_KCLASS_RESIDUAL, 2, st);
         if (hp == PDD)
             launch_residual_pairs((float2*)r, (const float2*)b, (const float2*)x, (const float2*)w.T64b, c->ld, m,
-                                  c->n, sigma, w.rpart, w.rblk, c->st);
+                                  c->n, sigma, w.rpart, w.rblk, st);
         else
-            launch_residual(r, b, x, w.T64b, c->ld, m, c->n, sigma, w.rpart, w.rblk, c->st);
-        launch_reduce_cols(w.rpart, w.rblk, m, w.norms, c->st);
+            launch_residual(r, b, x, w.T64b, c->ld, m, c->n, sigma, w.rpart, w.rblk, st);
+        launch_reduce_cols(w.rpart, w.rblk, m, w.norms, st);
     }
     // two stencils (m fields in and out, links once each) + b, x, Ax in, r out
     c->kbytes[DSBCG_KCLASS_RESIDUAL] +=
         ((c->schur ? 14.0 : 8.0) * m * c->n + link_passes(c) * 36 * c->V) * sizeof(double2);
-    CK(cudaMemcpyAsync(w.h_norms, w.norms, m * sizeof(double), cudaMemcpyDeviceToHost, c->st));
-    CK(cudaStreamSynchronize(c->st));
+    CK(cudaMemcpyAsync(w.h_norms, w.norms, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (idle) {
+        for (;;) {
+            const cudaError_t e = cudaStreamQuery(st);
+            if (e == cudaSuccess) break;
+            if (e != cudaErrorNotReady) CK(e);
+            cudaGetLastError();
+            CKS((*idle)());
+        }
+    }
+    CK(cudaStreamSynchronize(st));
     for (int i = 0; i < m; ++i) h_out[i] = w.h_norms[i];
     return DSBCG_OK;
 }
@@ -577,24 +598,40 @@ dsbcg_status lane_start(dsbcg_ctx* c, Lane& L, const void* rhs, int rhs_prec, si
     CK(cudaMemsetAsync(L.conv_step, 0xff, (size_t)s_in * m_in * sizeof(int), st));
     CK(cudaMemsetAsync(L.Xin, 0, (size_t)s_in * m_in * wb, st));
     // a0: G0 = B^H B (in the right-hand sides' precision), pivoted Cholesky
-    // with deflation, V_1 = B S0
+    // with deflation, V_1 = B S0.  A reduced-storage inner solve takes its
+    // Gram and basis from an FP32 copy of FP64 right-hand sides, like every
+    // other Gram of the solve (storage-precision fields, FP64 reduction and
+    // m x m work): an FP64 Gram would be bound by the FP64 pipe (1/64 rate).
+    // The lane's P block (work precision FP32, first written by step 1's
+    // shift update, which starts from V_1) holds the copy.
+    const void* grhs = rhs;
+    int gprec = rhs_prec;
+    size_t gld = rhs_ld;
+    if (rhs_prec == P64 && prec != P64) {
+        Prof p(c, DSBCG_KCLASS_OTHER, 1, st);
+        launch_convert_64_32((float2*)L.P, ld, (const double2*)rhs, rhs_ld, m_in, n, st);
+        c->kbytes[DSBCG_KCLASS_OTHER] += (double)m_in * n * (16.0 + 8.0);
+        grhs = L.P;
+        gprec = P32;
+        gld = ld;
+    }
     {
         Prof p(c, DSBCG_KCLASS_GRAM, 1, st);
-        launch_gram(rhs_prec, rhs, rhs, rhs_ld, n, nullptr, m_in, m_in, 1, 1, L.partials, L.nblk, 1.f, st);
+        launch_gram(gprec, grhs, grhs, gld, n, nullptr, m_in, m_in, 1, 1, L.partials, L.nblk, 1.f, st);
     }
     {
         Prof p(c, DSBCG_KCLASS_SMALL, 2, st);
-        launch_gram_reduce(L.partials, L.nblk, m_in, 1, 1, L.G, L.diag, nullptr, m_in, rhs_prec != P64, st);
+        launch_gram_reduce(L.partials, L.nblk, m_in, 1, 1, L.G, L.diag, nullptr, m_in, gprec != P64, st);
         launch_small_init(L.ss, L.ctl, L.G, L.diag, m_in, s_in, dtol, sfp64, st);
     }
     char* ring = (char*)L.vring;
     {
         Prof p(c, DSBCG_KCLASS_OTHER, 1, st);
-        launch_init_basis(prec, ring + 1 * (size_t)m_in * fb, ld, rhs, rhs_prec, rhs_ld, n, small_state_S(L.ss),
+        launch_init_basis(prec, ring + 1 * (size_t)m_in * fb, ld, grhs, gprec, gld, n, small_state_S(L.ss),
                           !sfp64, L.ctl, m_in, c->hscale, st);
     }
-    c->kbytes[DSBCG_KCLASS_GRAM] += (double)m_in * n * prec_elem_bytes(rhs_prec);
-    c->kbytes[DSBCG_KCLASS_OTHER] += (double)m_in * n * (prec_elem_bytes(rhs_prec) + prec_elem_bytes(prec));
+    c->kbytes[DSBCG_KCLASS_GRAM] += (double)m_in * n * prec_elem_bytes(gprec);
+    c->kbytes[DSBCG_KCLASS_OTHER] += (double)m_in * n * (prec_elem_bytes(gprec) + prec_elem_bytes(prec));
     CK(cudaGetLastError());
     L.m_in = m_in;
     L.s_in = s_in;
@@ -656,6 +693,7 @@ dsbcg_status lane_enqueue(dsbcg_ctx* c, Lane& L) {
     }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(L.h_ctl, L.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    if (L.h_active) CK(cudaMemcpyAsync(L.h_active, L.active, (size_t)s_in * sizeof(int), cudaMemcpyDeviceToHost, st));
     return DSBCG_OK;
 }
 
@@ -696,7 +734,9 @@ dsbcg_status lane_finish(dsbcg_ctx* c, Lane& L, InnerResult* out, int step_offse
     const Ctl& h = *L.h_ctl;
     {
         const double eb = (double)prec_elem_bytes(prec) * n, wbn = (double)prec_elem_bytes(wp) * n;
-        const double links = 36.0 * c->V * (double)prec_elem_bytes(prec);
+        // link entries read per stencil pass: 24 V with 12-real links (the
+        // normal operator's FP32 / 16-bit stencil), else 36 V
+        const double links = ((c->links12[prec] && !c->schur) ? 24.0 : 36.0) * c->V * (double)prec_elem_bytes(prec);
         // the Schur operator's four passes move 10 half fields per block
         // column (the counter counts the normal operator's 4)
         c->kbytes[DSBCG_KCLASS_DSLASH] += h.f_dslash * eb * (c->schur ? 2.5 : 1.0) + link_passes(c) * h.last_step * links;
@@ -936,6 +976,24 @@ dsbcg_status solve_core(dsbcg_ctx* c, int m, const void* B, int nbb, int s, cons
             CK(cudaMemcpyAsync(dst + q * ld, src + (size_t)idx[q] * ld, db, cudaMemcpyDeviceToDevice, c->st));
         return DSBCG_OK;
     };
+    // while the host waits for a true residual: give every running restart
+    // lane whose enqueued batch has drained its next batch (finished lanes
+    // are left to the main loop)
+    const std::function<dsbcg_status()> service_lanes = [&]() -> dsbcg_status {
+        for (int l = lane_lo; l < lane_hi; ++l) {
+            Lane& L = w.lanes[l];
+            if (lane_j[l] < 0 || L.st == c->st || !L.running) continue;
+            const cudaError_t e = cudaStreamQuery(L.st);
+            if (e == cudaErrorNotReady) {
+                cudaGetLastError();
+                continue;
+            }
+            CK(e);
+            CKS(lane_poll(c, L));
+            if (L.running) CKS(lane_enqueue(c, L));
+        }
+        return DSBCG_OK;
+    };
     // residuals of queued shifts while a lane is free; restarts where needed
     auto feed = [&]() -> dsbcg_status {
         for (;;) {
@@ -963,13 +1021,13 @@ dsbcg_status solve_core(dsbcg_ctx* c, int m, const void* B, int nbb, int s, cons
             } else if (full[j]) {
                 cl.resize(m);
                 for (int i = 0; i < m; ++i) cl[i] = i;
-                CKS(true_residual(c, hp, w.R64, Bblk(j), Xj, m, sigma[j], r2.data()));
+                CKS(true_residual(c, hp, w.R64, Bblk(j), Xj, m, sigma[j], r2.data(), &service_lanes, c->st));
                 full[j] = 0;
                 mvms += (long long)cl.size();
             } else {
                 CKS(gather(w.Xg, Xj, cl));
                 CKS(gather(w.Bg, Bblk(j), cl));
-                CKS(true_residual(c, hp, w.R64, w.Bg, w.Xg, (int)cl.size(), sigma[j], r2.data()));
+                CKS(true_residual(c, hp, w.R64, w.Bg, w.Xg, (int)cl.size(), sigma[j], r2.data(), &service_lanes, c->st));
                 mvms += (long long)cl.size();
             }
             std::vector<int> next, src;        // unconverged columns; their rows of R64
@@ -1014,11 +1072,27 @@ dsbcg_status solve_core(dsbcg_ctx* c, int m, const void* B, int nbb, int s, cons
         for (int l = lane_lo; l < lane_hi; ++l)
             if (lane_j[l] >= 0) busy = true;
         if (!busy) break;
-        for (int l = lane_lo; l < lane_hi; ++l)
-            if (lane_j[l] >= 0) CKS(lane_poll(c, w.lanes[l]));
+        // service the lanes whose enqueued batch has drained, as soon as any
+        // has (non-blocking queries): a lane never waits for the host to
+        // finish waiting on a slower lane
+        std::vector<int> ready;
+        for (long spins = 0; ready.empty(); ++spins) {
+            for (int l = lane_lo; l < lane_hi; ++l) {
+                if (lane_j[l] < 0) continue;
+                const cudaError_t e = cudaStreamQuery(w.lanes[l].st);
+                if (e == cudaSuccess) {
+                    ready.push_back(l);
+                } else if (e == cudaErrorNotReady) {
+                    cudaGetLastError();
+                } else {
+                    CK(e);
+                }
+            }
+            if (ready.empty() && spins > 64) std::this_thread::yield();
+        }
+        for (int l : ready) CKS(lane_poll(c, w.lanes[l]));
         prof_collect(c);
-        for (int l = lane_lo; l < lane_hi; ++l) {
-            if (lane_j[l] < 0) continue;
+        for (int l : ready) {
             Lane& L = w.lanes[l];
             if (L.running) {
                 CKS(lane_enqueue(c, L));
@@ -1113,7 +1187,7 @@ void dsbcg_params_default(dsbcg_params* p) {
     p->dtol = 0.0;
     p->max_block_steps = 100000;
     p->max_restarts = 50;
-    p->restart_drop = 1e-6;
+    p->restart_drop = 1e-7;
     p->poll_every = 16;
     p->freeze_converged = 1;
     p->refine = 1;
@@ -1231,6 +1305,9 @@ void dsbcg_destroy(dsbcg_ctx* c) {
         if (c->links12[p]) cudaFree(c->links12[p]);
     }
     if (c->gauge64) cudaFree(c->gauge64);
+    if (c->rst) cudaStreamDestroy(c->rst);
+    if (c->ev_joint) cudaEventDestroy(c->ev_joint);
+    if (c->ev_ref) cudaEventDestroy(c->ev_ref);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     for (auto& k : c->ev_live) {
         cudaEventDestroy(k.a);

@@ -103,3 +103,17 @@ def test_links_off_su3_use_full_storage(storage):
                 assert err.max() < TOL[storage], (op, storage, err.max())
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("operator,per_apply", [("normal", 1), ("schur", 2)])
+def test_stencil_bench_tool(capsys, operator, per_apply):
+    """python -m paper_1205_0359_gb300.stencil_bench: one JSON line with the
+    stencil's time and rate; D is one launch (two half-lattice passes for
+    the Schur operator)."""
+    import json
+    from paper_1205_0359_gb300 import stencil_bench
+    stencil_bench.main(["--lattice", "4,4,4,8", "--fields", "3", "--storage", "fp32", "--reps", "2",
+                        "--operator", operator])
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["stencil_launches_per_apply"] == per_apply
+    assert line["ms_per_launch"] > 0 and line["GBps"] > 0 and 0 < line["frac_of_hbm"] < 2
