@@ -479,11 +479,12 @@ void pack_any(dsbcg_ctx* c, int p, void* dst, const double2* src, int m) {
     else
         launch_pack_fields(p, dst, c->ld, src, m, c->Vf, c->hscale, c->st);
 }
-void unpack_any(dsbcg_ctx* c, int p, double2* dst, const void* src, int m) {
+void unpack_any(dsbcg_ctx* c, int p, double2* dst, const void* src, int m, cudaStream_t st = nullptr) {
+    if (!st) st = c->st;
     if (p == PDD)
-        launch_unpack_pairs(dst, (const float2*)src, c->ld, m, c->Vf, c->st);
+        launch_unpack_pairs(dst, (const float2*)src, c->ld, m, c->Vf, st);
     else
-        launch_unpack_fields(p, dst, src, c->ld, m, c->Vf, c->hscale, c->st);
+        launch_unpack_fields(p, dst, src, c->ld, m, c->Vf, c->hscale, st);
 }
 
 // out = Dhat in (dag = 0) or Dhat^H in (dag = 1) on odd-parity half fields,
@@ -902,60 +903,12 @@ dsbcg_status solve_core(dsbcg_ctx* c, int m, const void* B, int nbb, int s, cons
     // planes of the double-float fields
     const int rprec = hp == PDD ? P32 : P64;
     const size_t rld = hp_ld(c, hp);
-    auto accumulate = [&](double2* y, const void* x, int nf) {
-        Prof p(c, DSBCG_KCLASS_OTHER);
-        if (hp == PDD)
-            launch_accumulate_pairs((float2*)y, ld, (const float2*)x, ld, nf, n, c->st);
-        else
-            launch_accumulate(work_prec(prec), y, ld, x, ld, nf, n, c->st);
-    };
     const double drop = mixed ? std::max(prm.restart_drop, 1e-12) : 0.0;
 
-    // --- joint inner solve on B for all shifts (not with an initial guess or
-    // per-shift right-hand sides: the shifts' residuals then differ, and each
-    // is restarted on its own)
-    // shifts whose X_j is still zero (per-shift right-hand sides): their
-    // first residual is b itself, no operator application needed
-    std::vector<char> xzero(s, (nbb > 1 && !prm.x0) ? 1 : 0);
-    if (!prm.x0 && nbb == 1) {
-        Range r_joint("joint block solve");
-        std::vector<double> tg((size_t)s * m);
-        for (int j = 0; j < s; ++j)
-            for (int i = 0; i < m; ++i) tg[(size_t)j * m + i] = std::max(drop * bn[i], 0.5 * tol * bn[i]);
-        InnerResult ir;
-        Lane* L0 = &w.lanes[0];
-        CKS(lane_start(c, *L0, w.B64, rprec, rld, m, sigma, s, tg.data(), prec, dtol, prm.max_block_steps,
-                       prm.freeze_converged, prm.poll_every, sfp64));
-        CKS(run_lanes(c, &L0, 1));
-        CKS(lane_finish(c, *L0, &ir, 0, conv.data()));
-        total_steps += ir.steps;
-        mvms += ir.mvms;
-        deflations += ir.deflations;
-        final_rank = ir.final_rank;
-        if (ir.status == DSBCG_ERR_NOT_HPD) return DSBCG_ERR_NOT_HPD;
-        if (ir.status != 0) return DSBCG_ERR_CUDA;
-        accumulate(w.X64, w.Xin, s * m);
-    }
-    // --- output of a finished shift: its X_j goes to the caller's buffer as
-    // soon as its last true residual is in (device or mapped pinned host
-    // memory; other host memory is staged at the end), so that the transfer
-    // overlaps the restarts of the other shifts
-    void* const xmap = (x_dev || !X) ? nullptr : mapped_host_ptr(X);
-    double2* const xout = x_dev ? (double2*)X : (double2*)xmap;
-    auto emit = [&](int j) {
-        if (!xout) return;
-        Prof p(c, DSBCG_KCLASS_OTHER);
-        unpack_any(c, hp, xout + (size_t)j * m * n, w.X64 + (size_t)j * m * ld, m);
-    };
-    // --- high-precision true residuals and per-shift restarts.  Each shift
-    // has a list of unconverged columns (initially all) and waits in a queue
-    // for its true residual, taken on the context's stream.  Columns still
-    // above tol become the right-hand sides of a restart of that shift (block
-    // CG on sigma_j I + A) on a free lane; lanes run concurrently on their
-    // own streams, and a finished restart's solution is added to X_j and the
-    // shift queued again, so residuals overlap the restarts still running.
-    // With profiling on, lane 0 alone on the context's stream (serial
-    // restarts, clean per-kernel timings); results are bitwise the same.
+    // --- lanes for the per-shift restarts (allocated before the joint solve
+    // starts, so that no allocation falls inside it).  With profiling on,
+    // lane 0 alone on the context's stream (serial restarts, clean
+    // per-kernel timings); results are bitwise the same.
     int lane_lo = 0, lane_hi = 1;                      // refinement lanes [lane_lo, lane_hi)
     if (prm.refine && !c->profiling && s > 1) {
         const int got = ensure_refine_lanes(c, 1 + std::min(s, 16));
@@ -964,22 +917,162 @@ dsbcg_status solve_core(dsbcg_ctx* c, int m, const void* B, int nbb, int s, cons
             lane_hi = got;
         }
     }
+    // --- joint inner solve on B for all shifts (not with an initial guess or
+    // per-shift right-hand sides: the shifts' residuals then differ, and each
+    // is restarted on its own)
+    // shifts whose X_j is still zero (per-shift right-hand sides): their
+    // first residual is b itself, no operator application needed
+    std::vector<char> xzero(s, (nbb > 1 && !prm.x0) ? 1 : 0);
+    const bool joint = !prm.x0 && nbb == 1;
+    // Early hand-off: a shift the joint solve has frozen (all its columns
+    // below their targets; the shift update skips it from then on) has its
+    // final inner iterate, so its true residual and restarts start while the
+    // joint solve continues for the other shifts.  That work runs on the
+    // refinement stream, and the restarts on their own lanes.
+    const bool early = joint && prm.freeze_converged && lane_lo == 1;
+    cudaStream_t fst = c->st;                          // residuals, gathers, accumulation, output
+    if (early) {
+        if (!c->rst) CK(cudaStreamCreateWithFlags(&c->rst, cudaStreamNonBlocking));
+        if (!c->ev_joint) CK(cudaEventCreateWithFlags(&c->ev_joint, cudaEventDisableTiming));
+        if (!c->ev_ref) CK(cudaEventCreateWithFlags(&c->ev_ref, cudaEventDisableTiming));
+        fst = c->rst;
+    }
+    // on every return: no work of this solve left in flight on the refinement
+    // stream or the restart lanes (an error may leave lanes running)
+    struct Quiesce {
+        dsbcg_ctx* c;
+        int lo, hi;
+        ~Quiesce() {
+            if (c->rst) cudaStreamSynchronize(c->rst);
+            for (int l = lo; l < hi; ++l)
+                if (c->ws.lanes[l].st != c->st) cudaStreamSynchronize(c->ws.lanes[l].st);
+        }
+    } quiesce{c, lane_lo, lane_hi};
+    auto accumulate = [&](double2* y, const void* x, int nf) {
+        Prof p(c, DSBCG_KCLASS_OTHER, 1, fst);
+        if (hp == PDD)
+            launch_accumulate_pairs((float2*)y, ld, (const float2*)x, ld, nf, n, fst);
+        else
+            launch_accumulate(work_prec(prec), y, ld, x, ld, nf, n, fst);
+    };
+    std::vector<int> conv_joint((size_t)s * m, -1);
+    Lane* L0 = &w.lanes[0];
+    bool joint_running = false;
+    std::vector<char> handed(s, 0);
+    std::deque<int> queue;
+    // shift j's inner iterate is final: add it to X_j and queue its residual
+    auto handoff = [&](int j) -> dsbcg_status {
+        accumulate(w.X64 + (size_t)j * m * ld, (const char*)w.Xin + (size_t)j * m * ld * prec_elem_bytes(work_prec(prec)), m);
+        handed[j] = 1;
+        queue.push_back(j);
+        return DSBCG_OK;
+    };
+    auto joint_done = [&]() -> dsbcg_status {
+        InnerResult ir;
+        CKS(lane_finish(c, *L0, &ir, 0, conv_joint.data()));
+        joint_running = false;
+        total_steps += ir.steps;
+        mvms += ir.mvms;
+        deflations += ir.deflations;
+        final_rank = ir.final_rank;
+        if (ir.status == DSBCG_ERR_NOT_HPD) return DSBCG_ERR_NOT_HPD;
+        if (ir.status != 0) return DSBCG_ERR_CUDA;
+        return DSBCG_OK;
+    };
+    if (joint) {
+        Range r_joint("joint block solve");
+        std::vector<double> tg((size_t)s * m);
+        for (int j = 0; j < s; ++j)
+            for (int i = 0; i < m; ++i) tg[(size_t)j * m + i] = std::max(drop * bn[i], 0.5 * tol * bn[i]);
+        CKS(lane_start(c, *L0, w.B64, rprec, rld, m, sigma, s, tg.data(), prec, dtol, prm.max_block_steps,
+                       prm.freeze_converged, prm.poll_every, sfp64));
+        if (early) {
+            // the refinement stream starts after everything the solve has
+            // enqueued on the context's stream so far
+            CK(cudaEventRecord(c->ev_joint, c->st));
+            CK(cudaStreamWaitEvent(c->rst, c->ev_joint, 0));
+            CKS(lane_enqueue(c, *L0));
+            joint_running = true;
+        } else {
+            CKS(run_lanes(c, &L0, 1));
+            CKS(joint_done());
+            accumulate(w.X64, w.Xin, s * m);
+            for (int j = 0; j < s; ++j) queue.push_back(j);
+        }
+    } else {
+        for (int j = 0; j < s; ++j) queue.push_back(j);
+    }
+    // joint lane whose enqueued batch has drained: hand off the shifts it has
+    // frozen and give it its next batch, or finish it and hand off the rest.
+    // `polled` tells whether the batch had drained.
+    auto service_joint = [&](bool* polled) -> dsbcg_status {
+        *polled = false;
+        if (!joint_running) return DSBCG_OK;
+        const cudaError_t e = cudaStreamQuery(c->st);
+        if (e == cudaErrorNotReady) {
+            cudaGetLastError();
+            return DSBCG_OK;
+        }
+        CK(e);
+        *polled = true;
+        CKS(lane_poll(c, *L0));
+        if (L0->running) {
+            bool any = false;
+            for (int j = 0; j < s; ++j) any |= !handed[j] && L0->h_active[j] == 0;
+            if (any) {
+                // the joint stream is idle here: the event orders the
+                // refinement stream after its last batch
+                CK(cudaEventRecord(c->ev_joint, c->st));
+                CK(cudaStreamWaitEvent(fst, c->ev_joint, 0));
+                for (int j = 0; j < s; ++j)
+                    if (!handed[j] && L0->h_active[j] == 0) CKS(handoff(j));
+            }
+            CKS(lane_enqueue(c, *L0));
+        } else {
+            CKS(joint_done());
+            CK(cudaEventRecord(c->ev_joint, c->st));
+            CK(cudaStreamWaitEvent(fst, c->ev_joint, 0));
+            for (int j = 0; j < s; ++j)
+                if (!handed[j]) CKS(handoff(j));
+        }
+        return DSBCG_OK;
+    };
+    // block steps so far, the running joint solve's included
+    auto steps_so_far = [&]() { return total_steps + (joint_running ? L0->step : 0); };
+    // --- output of a finished shift: its X_j goes to the caller's buffer as
+    // soon as its last true residual is in (device or mapped pinned host
+    // memory; other host memory is staged at the end), so that the transfer
+    // overlaps the restarts of the other shifts
+    void* const xmap = (x_dev || !X) ? nullptr : mapped_host_ptr(X);
+    double2* const xout = x_dev ? (double2*)X : (double2*)xmap;
+    auto emit = [&](int j) {
+        if (!xout) return;
+        Prof p(c, DSBCG_KCLASS_OTHER, 1, fst);
+        unpack_any(c, hp, xout + (size_t)j * m * n, w.X64 + (size_t)j * m * ld, m, fst);
+    };
+    // --- high-precision true residuals and per-shift restarts.  Each shift
+    // has a list of unconverged columns (initially all) and waits in a queue
+    // for its true residual, taken on the refinement stream.  Columns still
+    // above tol become the right-hand sides of a restart of that shift (block
+    // CG on sigma_j I + A) on a free lane; lanes run concurrently on their
+    // own streams, and a finished restart's solution is added to X_j and the
+    // shift queued again, so residuals overlap the restarts still running.
     std::vector<double> r2(m);
     std::vector<std::vector<int>> cols(s);
     std::vector<char> full(s, 1);           // residual of all m columns still to be taken
-    std::deque<int> queue;
-    for (int j = 0; j < s; ++j) queue.push_back(j);
     std::vector<int> lane_j(w.lanes.size(), -1);       // shift restarted on each lane
     std::vector<std::vector<double>> lane_tg(w.lanes.size());
     auto gather = [&](double2* dst, const double2* src, const std::vector<int>& idx) -> dsbcg_status {
         for (size_t q = 0; q < idx.size(); ++q)
-            CK(cudaMemcpyAsync(dst + q * ld, src + (size_t)idx[q] * ld, db, cudaMemcpyDeviceToDevice, c->st));
+            CK(cudaMemcpyAsync(dst + q * ld, src + (size_t)idx[q] * ld, db, cudaMemcpyDeviceToDevice, fst));
         return DSBCG_OK;
     };
-    // while the host waits for a true residual: give every running restart
-    // lane whose enqueued batch has drained its next batch (finished lanes
-    // are left to the main loop)
+    // while the host waits for a true residual: keep the joint lane and
+    // every running restart lane whose enqueued batch has drained supplied
+    // (finished restart lanes are left to the main loop)
     const std::function<dsbcg_status()> service_lanes = [&]() -> dsbcg_status {
+        bool polled;
+        CKS(service_joint(&polled));
         for (int l = lane_lo; l < lane_hi; ++l) {
             Lane& L = w.lanes[l];
             if (lane_j[l] < 0 || L.st == c->st || !L.running) continue;
@@ -1015,19 +1108,19 @@ dsbcg_status solve_core(dsbcg_ctx* c, int m, const void* B, int nbb, int s, cons
                     cl[i] = i;
                     r2[i] = bnorm(j, i) * bnorm(j, i);
                 }
-                CK(cudaMemcpyAsync(w.R64, Bblk(j), (size_t)m * db, cudaMemcpyDeviceToDevice, c->st));
+                CK(cudaMemcpyAsync(w.R64, Bblk(j), (size_t)m * db, cudaMemcpyDeviceToDevice, fst));
                 full[j] = 0;
                 xzero[j] = 0;
             } else if (full[j]) {
                 cl.resize(m);
                 for (int i = 0; i < m; ++i) cl[i] = i;
-                CKS(true_residual(c, hp, w.R64, Bblk(j), Xj, m, sigma[j], r2.data(), &service_lanes, c->st));
+                CKS(true_residual(c, hp, w.R64, Bblk(j), Xj, m, sigma[j], r2.data(), &service_lanes, fst));
                 full[j] = 0;
                 mvms += (long long)cl.size();
             } else {
                 CKS(gather(w.Xg, Xj, cl));
                 CKS(gather(w.Bg, Bblk(j), cl));
-                CKS(true_residual(c, hp, w.R64, w.Bg, w.Xg, (int)cl.size(), sigma[j], r2.data(), &service_lanes, c->st));
+                CKS(true_residual(c, hp, w.R64, w.Bg, w.Xg, (int)cl.size(), sigma[j], r2.data(), &service_lanes, fst));
                 mvms += (long long)cl.size();
             }
             std::vector<int> next, src;        // unconverged columns; their rows of R64
@@ -1041,7 +1134,7 @@ dsbcg_status solve_core(dsbcg_ctx* c, int m, const void* B, int nbb, int s, cons
                 }
             }
             cl.swap(next);
-            if (cl.empty() || !prm.refine || restarts >= prm.max_restarts || total_steps >= prm.max_block_steps) {
+            if (cl.empty() || !prm.refine || restarts >= prm.max_restarts || steps_so_far() >= prm.max_block_steps) {
                 emit(j);                        // X_j is final
                 continue;
             }
@@ -1054,12 +1147,13 @@ dsbcg_status solve_core(dsbcg_ctx* c, int m, const void* B, int nbb, int s, cons
                 tg[q] = std::max(drop * rel[(size_t)j * m + i] * bnorm(j, i), 0.5 * tol * bnorm(j, i));
             }
             CKS(gather(L.rhs, w.R64, src));
-            if (L.st != c->st) {
-                CK(cudaEventRecord(L.ready, c->st));
+            if (L.st != fst) {
+                CK(cudaEventRecord(L.ready, fst));
                 CK(cudaStreamWaitEvent(L.st, L.ready, 0));
             }
             CKS(lane_start(c, L, L.rhs, rprec, rld, mu, &sigma[j], 1, tg.data(), prec, dtol,
-                           std::max(1, prm.max_block_steps - total_steps), prm.freeze_converged, prm.poll_every, sfp64));
+                           std::max(1, prm.max_block_steps - steps_so_far()), prm.freeze_converged, prm.poll_every,
+                           sfp64));
             CKS(lane_enqueue(c, L));
             restarts += 1;
             lane_j[li] = j;
@@ -1068,15 +1162,17 @@ dsbcg_status solve_core(dsbcg_ctx* c, int m, const void* B, int nbb, int s, cons
     Range r_ref("per-shift restarts");
     CKS(feed());
     for (;;) {
-        bool busy = false;
+        bool busy = joint_running;
         for (int l = lane_lo; l < lane_hi; ++l)
             if (lane_j[l] >= 0) busy = true;
         if (!busy) break;
-        // service the lanes whose enqueued batch has drained, as soon as any
-        // has (non-blocking queries): a lane never waits for the host to
-        // finish waiting on a slower lane
+        // service the joint lane and the restart lanes whose enqueued batch
+        // has drained, as soon as any has (non-blocking queries): a lane
+        // never waits for the host to finish waiting on a slower lane
         std::vector<int> ready;
-        for (long spins = 0; ready.empty(); ++spins) {
+        for (long spins = 0;; ++spins) {
+            bool polled = false;
+            CKS(service_joint(&polled));
             for (int l = lane_lo; l < lane_hi; ++l) {
                 if (lane_j[l] < 0) continue;
                 const cudaError_t e = cudaStreamQuery(w.lanes[l].st);
@@ -1088,7 +1184,8 @@ dsbcg_status solve_core(dsbcg_ctx* c, int m, const void* B, int nbb, int s, cons
                     CK(e);
                 }
             }
-            if (ready.empty() && spins > 64) std::this_thread::yield();
+            if (polled || !ready.empty()) break;
+            if (spins > 64) std::this_thread::yield();
         }
         for (int l : ready) CKS(lane_poll(c, w.lanes[l]));
         prof_collect(c);
@@ -1101,7 +1198,7 @@ dsbcg_status solve_core(dsbcg_ctx* c, int m, const void* B, int nbb, int s, cons
             // restart finished: fold its solution into X_j
             const int j = lane_j[l];
             InnerResult ir;
-            CKS(lane_finish(c, L, &ir, total_steps, conv_tmp.data()));
+            CKS(lane_finish(c, L, &ir, steps_so_far(), conv_tmp.data()));
             total_steps += ir.steps;
             mvms += ir.mvms;
             deflations += ir.deflations;
@@ -1117,6 +1214,15 @@ dsbcg_status solve_core(dsbcg_ctx* c, int m, const void* B, int nbb, int s, cons
             queue.push_back(j);           // its new residual decides the next restart
         }
         CKS(feed());
+    }
+    // a column no restart reached keeps the step at which the joint solve
+    // froze it
+    for (size_t t = 0; t < conv.size(); ++t)
+        if (conv[t] < 0) conv[t] = conv_joint[t];
+    if (early) {
+        // the output stage below runs on the context's stream
+        CK(cudaEventRecord(c->ev_ref, c->rst));
+        CK(cudaStreamWaitEvent(c->st, c->ev_ref, 0));
     }
     for (double r : rel)
         if (!(r <= tol)) result = DSBCG_NOT_CONVERGED;

@@ -168,9 +168,12 @@ def test_w2_full_size_mixed(w2, fp64res):
 
 
 def test_concurrent_restarts_match_serial(w1):
-    """The per-shift restarts run concurrently on separate streams; with the
-    library's profiling on they run one after another.  Each restart only
-    touches its own lane's buffers, so X is bitwise the same either way."""
+    """The per-shift restarts run concurrently on separate streams, each
+    shift handed off as soon as the joint solve freezes it (its residuals
+    and restarts then overlap the joint solve of the other shifts); with the
+    library's profiling on everything runs one step after another.  Each
+    restart only touches its own lane's buffers and a frozen shift's inner
+    iterate no longer changes, so X is bitwise the same either way."""
     wl, Ad, Xd, ctx = w1
     B = torch.from_numpy(wl["B"]).to(DEV)
     Xc, stc = ctx.solve(B, wl["sigma"], 1e-10, storage="fp32")
