@@ -124,13 +124,16 @@ typedef struct {
     double kernel_bytes[8]; /* algorithmic HBM bytes per class: each operand field,
                                link and coefficient block read or written once per
                                launch, counted from the block widths of every step */
+    double kernel_flops[8]; /* algorithmic floating-point operations per class
+                               (a complex multiply-add counts 8), for the classes
+                               that are counted: the shift update; 0 elsewhere */
 } dsbcg_stats;
 
 /* kernel classes reported in dsbcg_stats.kernel_ms */
 #define DSBCG_KCLASS_DSLASH 0       /* Wilson hopping stencil */
 #define DSBCG_KCLASS_GRAM 1         /* tall-skinny Gram products */
-#define DSBCG_KCLASS_UPDATE 2       /* block update W = Y - V a - V' b^H (+ Gram) */
-#define DSBCG_KCLASS_SHIFT 3        /* fused shift update (V, P_j, X_j) */
+#define DSBCG_KCLASS_UPDATE 2       /* block update W = Y - V a - V' b^H and V' = W S */
+#define DSBCG_KCLASS_SHIFT 3        /* shift update of P_j, X_j over a chunk of steps */
 #define DSBCG_KCLASS_SMALL 4        /* FP64 m x m kernels */
 #define DSBCG_KCLASS_RESIDUAL 5     /* true residuals (FP64 or double-float) */
 #define DSBCG_KCLASS_OTHER 6

@@ -61,9 +61,11 @@ void launch_gram_reduce(const double* partials, int nblk, int nf_max, int herm, 
                                         int, const void*, const void*, float, cudaStream_t);                 \
     extern template void launch_ib_t<P>(void*, size_t, const void*, int, size_t, size_t, const double2*, int, \
                                         const Ctl*, int, float, cudaStream_t);                               \
-    extern template void launch_su_t<P>(void*, const void*, const void*, size_t, void*, void*, size_t, size_t,  \
-                                        int, int, Ctl*, int, const void*, const void*, const void*,           \
-                                        const int*, float, cudaStream_t);
+    extern template void launch_vu_t<P>(void*, const void*, size_t, size_t, const Ctl*, int, const void*,     \
+                                        float, cudaStream_t);                                                 \
+    extern template void launch_sc_t<P>(const void*, size_t, int, size_t, void*, void*, size_t, size_t, int,  \
+                                        int, Ctl*, int, int, int, const void*, const void*, const int*,       \
+                                        float, cudaStream_t);
 namespace blas_impl {
 EXTERN_P(P64)
 EXTERN_P(P32)
@@ -93,17 +95,27 @@ void launch_init_basis(int prec, void* V1, size_t ldv, const void* B, int bprec,
     }
 }
 
-void launch_shift_update(int prec, int wprec, void* Vnext, const void* W, const void* Vk, size_t ld, void* P,
-                         void* X, size_t ldw, size_t n, int s, int m, Ctl* ctl, int nf_max,
-                         const void* coefS, const void* coefU, const void* coefL, const int* active,
-                         float hscale, cudaStream_t st) {
-    (void)wprec;
+void launch_v_update(int prec, void* Vnext, const void* W, size_t ld, size_t n, const Ctl* ctl, int nf_max,
+                     const void* coefS, float hscale, cudaStream_t st) {
     switch (prec) {
-        case P64: launch_su_t<P64>(Vnext, W, Vk, ld, P, X, ldw, n, s, m, ctl, nf_max, coefS, coefU, coefL, active, hscale, st); break;
-        case P32: launch_su_t<P32>(Vnext, W, Vk, ld, P, X, ldw, n, s, m, ctl, nf_max, coefS, coefU, coefL, active, hscale, st); break;
-        case PBF16: launch_su_t<PBF16>(Vnext, W, Vk, ld, P, X, ldw, n, s, m, ctl, nf_max, coefS, coefU, coefL, active, hscale, st); break;
-        case PF16: launch_su_t<PF16>(Vnext, W, Vk, ld, P, X, ldw, n, s, m, ctl, nf_max, coefS, coefU, coefL, active, hscale, st); break;
+        case P64: launch_vu_t<P64>(Vnext, W, ld, n, ctl, nf_max, coefS, hscale, st); break;
+        case P32: launch_vu_t<P32>(Vnext, W, ld, n, ctl, nf_max, coefS, hscale, st); break;
+        case PBF16: launch_vu_t<PBF16>(Vnext, W, ld, n, ctl, nf_max, coefS, hscale, st); break;
+        case PF16: launch_vu_t<PF16>(Vnext, W, ld, n, ctl, nf_max, coefS, hscale, st); break;
     }
+}
+
+void launch_shift_chunk(int prec, const void* ring, size_t slot_elems, int R, size_t ld, void* P, void* X,
+                        size_t ldw, size_t n, int s, int m, Ctl* ctl, int nf_max, int k0, int C, const void* coefU,
+                        const void* coefL, const int* active, float hscale, cudaStream_t st) {
+#define SC_ARGS ring, slot_elems, R, ld, P, X, ldw, n, s, m, ctl, nf_max, k0, C, coefU, coefL, active, hscale, st
+    switch (prec) {
+        case P64: launch_sc_t<P64>(SC_ARGS); break;
+        case P32: launch_sc_t<P32>(SC_ARGS); break;
+        case PBF16: launch_sc_t<PBF16>(SC_ARGS); break;
+        case PF16: launch_sc_t<PF16>(SC_ARGS); break;
+    }
+#undef SC_ARGS
 }
 
 }  // namespace dsbcg

@@ -583,176 +583,133 @@ __global__ void __launch_bounds__(256) v_update_kernel(typename Tr<P>::S2* __res
     }
 }
 
-// Per-shift update of one row tile: X_j += P_j Ut_j, P_j <- V_{k+1} - P_j Lh_j.
-// One CTA per (row tile, shift), shift index fastest so that the CTAs that
-// read the same V_{k+1} tile run together and share it through L2.  The P_j
-// and X_j tiles (one contiguous run of ROWS elements per field) arrive in
-// shared memory by bulk asynchronous copies completing on one mbarrier;
-// V_{k+1} rows are read straight from L2, which keeps the shared memory per
-// CTA small and the resident CTAs per SM many.  Results are stored directly
-// (coalesced).  The mbarrier wait is bounded: on timeout the CTA records an
-// error in the control block and returns after draining its copies.  At
-// k == 1 the search block is P_j = V_1 (the current block, storage precision).
-template <int NF, int PW, int PS>
-__host__ __device__ constexpr size_t su_smem_bytes(int rows) {
-    return (size_t)rows * NF * 2 * sizeof(typename Tr<PW>::S2) + 2 * (size_t)NF * NF * sizeof(typename Tr<PW>::C) + 16;
+// Per-shift update over a chunk of block steps k0+1 .. k0+C, one thread per
+// (row, shift): for each step k of the chunk in which shift j is active,
+//     X_j += P_j Ut_j^(k),   P_j <- V_{k+1} - P_j Lh_j^(k)
+// with P_j and X_j held in registers across the chunk, so that they cross
+// HBM once per chunk instead of once per step.  The arithmetic per element
+// is the per-step update's, in the same order; only the round trips of P_j
+// and X_j through memory (in their own precision, so without rounding) are
+// gone.  Inputs: the basis ring (slot k mod R holds V_k; V_1 is the search
+// block of step 1), the per-step coefficient tiles of every shift (slot
+// (k - 1) mod C), the per-step active flags and, in the control block, the
+// block widths of the last 16 steps.  Steps after the solve's last executed
+// step are skipped, so one launch at the end of a batch also closes a
+// shorter chunk.  One CTA per (row tile, shift), shift index fastest so that
+// the CTAs reading the same V rows run together and share them through L2.
+template <int NF, int PW>
+__host__ __device__ constexpr size_t sc_smem_bytes() {
+    return 4 * (size_t)NF * NF * sizeof(typename Tr<PW>::C);
 }
 
-// rows per thread of shift_tile_kernel: one (two rows per thread halve the
-// shared-memory coefficient reads but, at about 170 registers, cut the
-// resident warps from 28 to 10 per SM, which measured slower on GB300)
-__host__ __device__ constexpr int su_rpt(int, int) { return 1; }
-
 template <int P, int PW, int NF, int ROWS>
-__global__ void __launch_bounds__(ROWS / su_rpt(NF, PW)) shift_tile_kernel(
-    const typename Tr<P>::S2* __restrict__ Vn, const typename Tr<P>::S2* __restrict__ Vk, size_t ld,
+__global__ void __launch_bounds__(ROWS, (NF <= 12 && PW == P32) ? 4 : 1) shift_chunk_kernel(
+    const typename Tr<P>::S2* __restrict__ ring, size_t slot_elems, int R, size_t ld,
     typename Tr<PW>::S2* __restrict__ Pb, typename Tr<PW>::S2* __restrict__ Xb, size_t ldw, size_t n, int s, int m,
-    Ctl* __restrict__ ctl, const typename Tr<PW>::C* __restrict__ cU, const typename Tr<PW>::C* __restrict__ cL,
-    const int* __restrict__ active, float hscale) {
-    using C = typename Tr<PW>::C;
-    using R = typename Tr<PW>::R;
-    using E = typename Tr<PW>::S2;
+    Ctl* __restrict__ ctl, int k0, int C, const typename Tr<PW>::C* __restrict__ cU,
+    const typename Tr<PW>::C* __restrict__ cL, const int* __restrict__ act, float hscale) {
+    using C2 = typename Tr<PW>::C;
+    using R2 = typename Tr<PW>::R;
     using SE = typename Tr<P>::S2;
-    if (ctl->done) return;
     const int j = (int)(blockIdx.x % (unsigned)s);
-    if (!active[j]) return;
-    const int mk_ = ctl->mk, mn = ctl->mnext, k = ctl->k;
-    extern __shared__ __align__(128) unsigned char su_smem[];
-    E* sP = reinterpret_cast<E*>(su_smem);                          // [NF][ROWS] P_j (or V_1 at k == 1)
-    E* sX = sP + NF * ROWS;
-    C* sU = reinterpret_cast<C*>(sX + NF * ROWS);
-    C* sL = sU + NF * NF;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sL + NF * NF);
+    const int kend = min(k0 + C, ctl->last_step);
+    if (kend <= k0 || !act[(size_t)(k0 % C) * s + j]) return;
+    extern __shared__ __align__(16) unsigned char sc_smem[];
+    C2* sU = reinterpret_cast<C2*>(sc_smem);            // [2][NF * NF]
+    C2* sL = sU + 2 * NF * NF;                           // [2][NF * NF]
     const int tid = threadIdx.x;
     const size_t e0 = (size_t)(blockIdx.x / (unsigned)s) * ROWS;
-    const int rows = (int)((n - e0) < (size_t)ROWS ? (n - e0) : (size_t)ROWS);
-    const uint32_t tb = (uint32_t)rows * sizeof(E), tbs = (uint32_t)rows * sizeof(SE);
-    const E* Pj = Pb + (size_t)j * m * ldw + e0;
-    E* Pjw = Pb + (size_t)j * m * ldw + e0;
-    E* Xj = Xb + (size_t)j * m * ldw + e0;
-    if (tid == 0) {
-        mbar_init(bar, 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
-    if (tid == 0) {
-        // k == 1: the search block is V_1 itself (loaded into sP's place)
-        const uint32_t nv = k == 1 ? (uint32_t)mk_ : 0u;
-        const uint32_t np = k > 1 ? (uint32_t)mk_ : 0u;
-        mbar_expect_tx(bar, nv * tbs + (np + (uint32_t)m) * tb);
-        if (k == 1) {
-            // V_1 (storage precision) into the P tile's space, which is at least as large
-            for (int a = 0; a < mk_; ++a) bulk_g2s(reinterpret_cast<SE*>(sP) + a * ROWS, Vk + (size_t)a * ld + e0, tbs, bar);
-        } else {
-            for (int a = 0; a < mk_; ++a) bulk_g2s(sP + a * ROWS, Pj + (size_t)a * ldw, tb, bar);
-        }
-        for (int i = 0; i < m; ++i) bulk_g2s(sX + i * ROWS, Xj + (size_t)i * ldw, tb, bar);
-    }
-    for (int t = tid; t < NF * NF; t += ROWS / su_rpt(NF, PW)) {
-        sU[t] = cU[((size_t)j * M_MAX + t / NF) * M_MAX + t % NF];
-        sL[t] = cL[((size_t)j * M_MAX + t / NF) * M_MAX + t % NF];
-    }
-    const bool ok = mbar_wait(bar, 0);
-    __syncthreads();
-    if (!__syncthreads_and(ok)) {
-        if (tid == 0) {
-            mbar_wait(bar, 0);
-            atomicCAS(&ctl->status, 0, ST_WAIT_TIMEOUT);
-        }
-        return;
-    }
+    const bool ok = e0 + tid < n;
+    const size_t e = e0 + (ok ? tid : 0);
     const float inv = (P == PBF16 || P == PF16) ? 1.f / hscale : 1.f;
-    auto ldv = [&](const SE* base, int c, int r) -> C {
-        auto q = Elem<P>::ld(base, (size_t)c * ROWS + r, inv);
-        return mk(R(q.x), R(q.y));
+    auto ldv = [&](int k, int c) -> C2 {
+        const auto q = Elem<P>::ld(ring + (size_t)(k % R) * slot_elems + (size_t)c * ld, e, inv);
+        return mk(R2(q.x), R2(q.y));
     };
-    // RPT rows per thread (r = tid, tid + ROWS / RPT, ...): every coefficient
-    // read from shared memory serves all of them, and FP32 coefficients are
-    // read two at a time; each element accumulates over a in ascending order
-    constexpr int RPT = su_rpt(NF, PW), TPB = ROWS / RPT;
-    int rr_[RPT];
-    bool ok_[RPT];
+    const size_t tile = (size_t)M_MAX * M_MAX;
+    typename Tr<PW>::S2* Pj = Pb + (size_t)j * m * ldw;
+    typename Tr<PW>::S2* Xj = Xb + (size_t)j * m * ldw;
+    int mk_ = ctl->hmk[k0 & (CTL_HIST - 1)];
+    C2 t[NF], x[NF];
 #pragma unroll
-    for (int q = 0; q < RPT; ++q) {
-        rr_[q] = tid + q * TPB;
-        ok_[q] = rr_[q] < rows;
+    for (int a = 0; a < NF; ++a) {
+        if (a < mk_) t[a] = (k0 == 0) ? ldv(1, a) : Pj[(size_t)a * ldw + e];
+        else t[a] = mk(R2(0), R2(0));
+        x[a] = a < m ? Xj[(size_t)a * ldw + e] : mk(R2(0), R2(0));
     }
-    C t[RPT][NF], x[RPT][NF];
-#pragma unroll
-    for (int q = 0; q < RPT; ++q)
+    int mn = mk_;
+    int k = k0 + 1;
+    for (; k <= kend; ++k) {
+        const int q = (k - 1) % C;
+        if (!act[(size_t)q * s + j]) break;
+        mn = ctl->hmn[(k - 1) & (CTL_HIST - 1)];
+        // this step's tiles into buffer b; the sync also orders the reads of
+        // step k - 2 (same buffer) before the writes
+        const int b = (k - k0) & 1;
+        C2* bU = sU + b * NF * NF;
+        C2* bL = sL + b * NF * NF;
+        const C2* gU = cU + ((size_t)q * s + j) * tile;
+        const C2* gL = cL + ((size_t)q * s + j) * tile;
+        for (int u = tid; u < NF * NF; u += ROWS) {
+            bU[u] = gU[(u / NF) * M_MAX + u % NF];
+            bL[u] = gL[(u / NF) * M_MAX + u % NF];
+        }
+        __syncthreads();
+        // X_j += P_j Ut_j
 #pragma unroll
         for (int a = 0; a < NF; ++a) {
-            const int r = ok_[q] ? rr_[q] : 0;
-            if (a < mk_) t[q][a] = (k == 1) ? ldv(reinterpret_cast<const SE*>(sP), a, r) : sP[a * ROWS + r];
-            else t[q][a] = mk(R(0), R(0));
-            x[q][a] = a < m ? sX[a * ROWS + r] : mk(R(0), R(0));
-        }
-    // X_j += P_j Ut_j
 #pragma unroll
-    for (int a = 0; a < NF; ++a) {
-#pragma unroll
-        for (int i = 0; i < NF; i += 2) {
-            C u0, u1;
-            if constexpr (sizeof(C) == 8) {
-                const float4 u2 = *reinterpret_cast<const float4*>(&sU[a * NF + i]);
-                u0 = mk(R(u2.x), R(u2.y));
-                u1 = mk(R(u2.z), R(u2.w));
-            } else {
-                u0 = sU[a * NF + i];
-                u1 = sU[a * NF + i + 1];
-            }
-#pragma unroll
-            for (int q = 0; q < RPT; ++q) {
-                cfma(x[q][i], t[q][a], u0);
-                cfma(x[q][i + 1], t[q][a], u1);
+            for (int i = 0; i < NF; i += 2) {
+                C2 u0, u1;
+                if constexpr (sizeof(C2) == 8) {
+                    const float4 u2 = *reinterpret_cast<const float4*>(&bU[a * NF + i]);
+                    u0 = mk(R2(u2.x), R2(u2.y));
+                    u1 = mk(R2(u2.z), R2(u2.w));
+                } else {
+                    u0 = bU[a * NF + i];
+                    u1 = bU[a * NF + i + 1];
+                }
+                cfma(x[i], t[a], u0);
+                cfma(x[i + 1], t[a], u1);
             }
         }
+        // P_j <- V_{k+1} - P_j Lh_j
+        C2 pn[NF];
+#pragma unroll
+        for (int c = 0; c < NF; ++c) pn[c] = c < mn ? ldv(k + 1, c) : mk(R2(0), R2(0));
+#pragma unroll
+        for (int a = 0; a < NF; ++a) {
+#pragma unroll
+            for (int c = 0; c < NF; c += 2) {
+                C2 l0, l1;
+                if constexpr (sizeof(C2) == 8) {
+                    const float4 l2 = *reinterpret_cast<const float4*>(&bL[a * NF + c]);
+                    l0 = mk(R2(l2.x), R2(l2.y));
+                    l1 = mk(R2(l2.z), R2(l2.w));
+                } else {
+                    l0 = bL[a * NF + c];
+                    l1 = bL[a * NF + c + 1];
+                }
+                cfms(pn[c], t[a], l0);
+                cfms(pn[c + 1], t[a], l1);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < NF; ++c) t[c] = c < mn ? pn[c] : mk(R2(0), R2(0));
     }
+    if (ok) {
 #pragma unroll
-    for (int q = 0; q < RPT; ++q)
-        if (ok_[q])
+        for (int i = 0; i < NF; ++i)
+            if (i < m) Xj[(size_t)i * ldw + e] = x[i];
 #pragma unroll
-            for (int i = 0; i < NF; ++i)
-                if (i < m) Xj[(size_t)i * ldw + rr_[q]] = x[q][i];
-    // P_j <- V_{k+1} - P_j Lh_j
-    C pn[RPT][NF];
-#pragma unroll
-    for (int q = 0; q < RPT; ++q)
-#pragma unroll
-        for (int c = 0; c < NF; ++c) {
-            if (c < mn) {
-                const auto v = Elem<P>::ld(Vn + (size_t)c * ld, e0 + (ok_[q] ? rr_[q] : 0), inv);
-                pn[q][c] = mk(R(v.x), R(v.y));
-            } else {
-                pn[q][c] = mk(R(0), R(0));
-            }
-        }
-#pragma unroll
-    for (int a = 0; a < NF; ++a) {
-#pragma unroll
-        for (int c = 0; c < NF; c += 2) {
-            C l0, l1;
-            if constexpr (sizeof(C) == 8) {
-                const float4 l2 = *reinterpret_cast<const float4*>(&sL[a * NF + c]);
-                l0 = mk(R(l2.x), R(l2.y));
-                l1 = mk(R(l2.z), R(l2.w));
-            } else {
-                l0 = sL[a * NF + c];
-                l1 = sL[a * NF + c + 1];
-            }
-#pragma unroll
-            for (int q = 0; q < RPT; ++q) {
-                cfms(pn[q][c], t[q][a], l0);
-                cfms(pn[q][c + 1], t[q][a], l1);
-            }
-        }
+        for (int c = 0; c < NF; ++c)
+            if (c < mn) Pj[(size_t)c * ldw + e] = t[c];
     }
-#pragma unroll
-    for (int q = 0; q < RPT; ++q)
-        if (ok_[q])
-#pragma unroll
-            for (int c = 0; c < NF; ++c)
-                if (c < mn) Pjw[(size_t)c * ldw + rr_[q]] = pn[q][c];
+    if (blockIdx.x < (unsigned)s && tid == 0) {
+        // work-precision fields moved: P_j (or V_1) and X_j in, X_j and P_j out
+        atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->f_shift_w),
+                  (unsigned long long)(mk_ + 2 * m + mn));
+    }
 }
 
 inline int nf_bucket(int nf) { return nf <= 4 ? 4 : nf <= 8 ? 8 : nf <= 12 ? 12 : nf <= 16 ? 16 : nf <= 24 ? 24 : 32; }
@@ -804,28 +761,40 @@ void launch_ib_t(void* V1, size_t ldv, const void* B, int bprec, size_t ldb, siz
 }
 
 template <int P>
-void launch_su_t(void* Vnext, const void* W, const void* Vk, size_t ld, void* Pp, void* X, size_t ldw, size_t n,
-                 int s, int m, Ctl* ctl, int nf_max, const void* coefS, const void* coefU, const void* coefL,
+void launch_vu_t(void* Vnext, const void* W, size_t ld, size_t n, const Ctl* ctl, int nf_max, const void* coefS,
+                 float hscale, cudaStream_t st) {
+    constexpr int PW = (P == P64) ? P64 : P32;
+    using S2 = typename Tr<P>::S2;
+    using CW = typename Tr<PW>::C;
+#define BI_VU(NF)                                                                                           \
+    v_update_kernel<P, NF><<<(unsigned)((n + 255) / 256), 256, 0, st>>>((S2*)Vnext, (const S2*)W, ld, n, ctl, \
+                                                                       (const CW*)coefS, hscale)
+    BI_DISPATCH_NF(nf_max, BI_VU)
+#undef BI_VU
+}
+
+template <int P>
+void launch_sc_t(const void* ring, size_t slot_elems, int R, size_t ld, void* Pp, void* X, size_t ldw, size_t n,
+                 int s, int m, Ctl* ctl, int nf_max, int k0, int C, const void* coefU, const void* coefL,
                  const int* active, float hscale, cudaStream_t st) {
     constexpr int PW = (P == P64) ? P64 : P32;
     using S2 = typename Tr<P>::S2;
     using W2 = typename Tr<PW>::S2;
     using CW = typename Tr<PW>::C;
-#define BI_SU(NF)                                                                                           \
+#define BI_SC(NF)                                                                                           \
     {                                                                                                       \
-        constexpr int ROWS = su_smem_bytes<NF, PW, P>(128) <= 200000 ? 128 : 64;                            \
-        v_update_kernel<P, NF><<<(unsigned)((n + 255) / 256), 256, 0, st>>>((S2*)Vnext, (const S2*)W, ld, n, ctl, \
-                                                                           (const CW*)coefS, hscale);       \
-        constexpr size_t SMEM = su_smem_bytes<NF, PW, P>(ROWS);                                             \
+        constexpr int ROWS = 128;                                                                           \
+        constexpr size_t SMEM = sc_smem_bytes<NF, PW>();                                                    \
         static std::atomic<unsigned long long> devs{0};                                                     \
-        max_dyn_smem_once(shift_tile_kernel<P, PW, NF, ROWS>, (int)SMEM, devs);                             \
+        max_dyn_smem_once(shift_chunk_kernel<P, PW, NF, ROWS>, (int)SMEM, devs);                            \
         const unsigned g = (unsigned)(((n + ROWS - 1) / ROWS) * (size_t)s);                                 \
-        shift_tile_kernel<P, PW, NF, ROWS><<<g, ROWS / su_rpt(NF, PW), SMEM, st>>>(                                          \
-            (const S2*)Vnext, (const S2*)Vk, ld, (W2*)Pp, (W2*)X, ldw, n, s, m, ctl, (const CW*)coefU,      \
-            (const CW*)coefL, active, hscale);                                                              \
+        shift_chunk_kernel<P, PW, NF, ROWS><<<g, ROWS, SMEM, st>>>((const S2*)ring, slot_elems, R, ld, (W2*)Pp, \
+                                                                   (W2*)X, ldw, n, s, m, ctl, k0, C,        \
+                                                                   (const CW*)coefU, (const CW*)coefL, active, \
+                                                                   hscale);                                 \
     }
-    BI_DISPATCH_NF(nf_max, BI_SU)
-#undef BI_SU
+    BI_DISPATCH_NF(nf_max, BI_SC)
+#undef BI_SC
 }
 
 #define BI_INSTANTIATE(P)                                                                                  \
@@ -833,9 +802,10 @@ void launch_su_t(void* Vnext, const void* W, const void* Vk, size_t ld, void* Pp
                                  const void*, const void*, float, cudaStream_t);                          \
     template void launch_ib_t<P>(void*, size_t, const void*, int, size_t, size_t, const double2*, int,       \
                                  const Ctl*, int, float, cudaStream_t);                                    \
-    template void launch_su_t<P>(void*, const void*, const void*, size_t, void*, void*, size_t, size_t, int, int, \
-                                 Ctl*, int, const void*, const void*, const void*, const int*, float,         \
-                                 cudaStream_t);
+    template void launch_vu_t<P>(void*, const void*, size_t, size_t, const Ctl*, int, const void*, float,    \
+                                 cudaStream_t);                                                            \
+    template void launch_sc_t<P>(const void*, size_t, int, size_t, void*, void*, size_t, size_t, int, int,   \
+                                 Ctl*, int, int, int, const void*, const void*, const int*, float, cudaStream_t);
 
 }  // namespace blas_impl
 }  // namespace dsbcg

@@ -52,6 +52,7 @@ inline void max_dyn_smem_once(F* func, int bytes, std::atomic<unsigned long long
 }
 
 constexpr int M_MAX = 32;      // largest block width (right-hand sides in a block)
+constexpr int CTL_HIST = 16;   // block widths kept per step (the longest shift-update chunk)
 constexpr int S_MAX = 64;      // largest number of shifts
 
 // ------------------------------------------------------------------ traits --
@@ -285,14 +286,17 @@ struct Ctl {
     int deflations;   // directions dropped so far
     long long mvms;   // single-vector A applications
     int last_step;    // last step that did work
-    int pad[5];
+    int hmk[CTL_HIST];  // width of V_k for step k at slot (k - 1) mod CTL_HIST
+    int hmn[CTL_HIST];  // width of V_{k+1} for step k, same slots
+    int pad[1];
     // algorithmic traffic, in fields (one complex n-vector) moved to or from
     // HBM, summed over block steps by the step's last kernel:
     long long f_dslash;   // storage-precision fields read + written by the 2 stencils
     long long f_gram;     // storage-precision fields read by the 2 Gram products
     long long f_update;   // storage-precision fields of the block update
-    long long f_shift_s;  // storage-precision fields of the shift update (W in, V out)
-    long long f_shift_w;  // work-precision fields of the shift update (P_j, X_j)
+    long long f_shift_s;  // storage-precision fields read by the shift update (V_{k+1}, once per step)
+    long long f_shift_w;  // work-precision fields of the shift update (P_j, X_j: once per chunk)
+    long long f_shift_cmac;  // complex multiply-adds per element of the shift update
 };
 
 // error codes mirrored from dsbcg.h

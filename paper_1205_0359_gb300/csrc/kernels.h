@@ -109,14 +109,20 @@ void launch_block_update(int prec, void* W, const void* Y, const void* Vk, const
 // or double-float when s_dd)
 void launch_init_basis(int prec, void* V1, size_t ldv, const void* B, int bprec, size_t ldb, size_t n,
                        const double2* S, int s_dd, const Ctl* ctl, int nf_in, float hscale, cudaStream_t st);
-// shift update (the per-shift short recurrences, Sec. 3): V_{k+1} = W S;
-// for active shifts X_j += P_j Ut_j and P_j <- V_{k+1} - P_j LhT_j.  P and X
-// hold s blocks of m fields of ldw elements (field-major, like every other
-// block).
-void launch_shift_update(int prec, int wprec, void* Vnext, const void* W, const void* Vk,
-                         size_t ld, void* P, void* X, size_t ldw, size_t n, int s, int m,
-                         Ctl* ctl, int nf_max, const void* coefS, const void* coefU,
-                         const void* coefL, const int* active, float hscale, cudaStream_t st);
+// V_{k+1} = W S (S from the step's QR, M_MAX-strided work-precision tile)
+void launch_v_update(int prec, void* Vnext, const void* W, size_t ld, size_t n, const Ctl* ctl, int nf_max,
+                     const void* coefS, float hscale, cudaStream_t st);
+// shift update (the per-shift short recurrences, Sec. 3) over the block
+// steps k0+1 .. min(k0 + C, last executed step): for every step in which
+// shift j is active, X_j += P_j Ut_j and P_j <- V_{k+1} - P_j LhT_j, with P_j
+// and X_j kept on chip across the steps.  ring: R slots of slot_elems
+// storage-precision elements, slot k mod R holding V_k (V_1 is the search
+// block of step 1).  coefU / coefL: per step slot (k - 1) mod C, s tiles of
+// M_MAX x M_MAX work-precision entries; active: per step slot, s flags.  P
+// and X hold s blocks of m fields of ldw elements (field-major).
+void launch_shift_chunk(int prec, const void* ring, size_t slot_elems, int R, size_t ld, void* P, void* X,
+                        size_t ldw, size_t n, int s, int m, Ctl* ctl, int nf_max, int k0, int C, const void* coefU,
+                        const void* coefL, const int* active, float hscale, cudaStream_t st);
 
 // ---- small.cu ---------------------------------------------------------------
 struct SmallState;     // device m x m state (FP64 or double-float), defined in small.cu

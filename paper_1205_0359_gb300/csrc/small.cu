@@ -509,7 +509,7 @@ __global__ void small_init_kernel(SmallStateT<T>* ss, Ctl* ctl, const double2* _
         ctl->deflations = m - r;
         ctl->mvms = 0;
         ctl->last_step = 0;
-        ctl->f_dslash = ctl->f_gram = ctl->f_update = ctl->f_shift_s = ctl->f_shift_w = 0;
+        ctl->f_dslash = ctl->f_gram = ctl->f_update = ctl->f_shift_s = ctl->f_shift_w = ctl->f_shift_cmac = 0;
     }
 }
 
@@ -701,9 +701,11 @@ __global__ void small_finish_kernel(SmallState* ss, Ctl* ctl, int s, int m, cons
         ctl->mvms += mk_;
         ctl->f_dslash += 4LL * mk_;                 // D: V in, Z out; D^H: Z in, Y out
         ctl->f_gram += 3LL * mk_;                   // V, Y for alpha; W for W^H W
-        ctl->f_update += 3LL * mk_ + mp;            // Y, V_k, V_{k-1} in, W out
-        ctl->f_shift_s += (long long)mk_ + mn;      // W in, V_{k+1} out
-        ctl->f_shift_w += (long long)nkd * (mk_ + mn + 2 * m);   // P_j in/out, X_j in/out
+        ctl->f_update += 3LL * mk_ + mp + mk_ + mn; // Y, V_k, V_{k-1} in, W out; V_{k+1} = W S
+        if (nkd > 0) ctl->f_shift_s += mn;          // V_{k+1} rows, read once per row tile
+        ctl->f_shift_cmac += (long long)nkd * mk_ * (m + mn);   // X_j += P_j Ut_j, P_j <- V - P_j Lh_j
+        ctl->hmk[(ctl->k - 1) & (CTL_HIST - 1)] = mk_;
+        ctl->hmn[(ctl->k - 1) & (CTL_HIST - 1)] = mn;
         ctl->last_step = ctl->k;
         ctl->nact = nalive;
         ctl->k += 1;

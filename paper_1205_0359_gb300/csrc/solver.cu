@@ -84,6 +84,10 @@ struct Lane {
     int* h_active = nullptr;                      // pinned (joint lane): shifts updated in the last step
     // the inner solve in progress
     int m_in = 0, s_in = 0, prec = 0, step = 0, max_steps = 0, freeze = 0, poll_every = 1;
+    // block steps per shift-update chunk (the basis ring holds chunk + 1
+    // blocks; coefficient tiles and active flags chunk slots) and the last
+    // step already folded into P and X
+    int chunk = 1, k0 = 0;
     int sfp64 = 1;                                // m x m scalar: FP64 (1) or double-float (0)
     double dtol = 0;
     bool running = false;
@@ -117,6 +121,7 @@ struct dsbcg_ctx {
     double kms[8] = {0};
     long long klaunch[8] = {0};
     double kbytes[8] = {0};
+    double kflops[8] = {0};
     // workspace
     std::vector<void*> allocs;
     struct WS {
@@ -212,6 +217,11 @@ dsbcg_status dmalloc(dsbcg_ctx* c, void** p, size_t bytes) {
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        cudaGetLastError();
+        fprintf(stderr, "dsbcg: device allocation of %zu bytes failed (%s; %zu of %zu bytes free)\n", bytes,
+                cudaGetErrorString(e), fr, tot);
         return DSBCG_ERR_OOM;
     }
     c->ws.mem.push_back(*p);
@@ -256,6 +266,21 @@ dsbcg_status ensure_links(dsbcg_ctx* c, int prec) {
     return DSBCG_OK;
 }
 
+// Block steps per shift-update chunk for a lane whose basis blocks take
+// block_bytes: cmax (a power of two, at most CTL_HIST), halved while the
+// ring of chunk + 1 blocks would take more than 1/frac of the device memory
+// (at least 1: the per-step update with a two-block ring).
+int chunk_steps(size_t block_bytes, int cmax, size_t frac) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    int C = std::min(cmax, CTL_HIST);
+    while (C > 1 && (size_t)(C + 1) * block_bytes > tot / frac) C /= 2;
+    return C;
+}
+
 dsbcg_status ensure_ws(dsbcg_ctx* c, int m, int s, int prec, int nbb) {
     auto& w = c->ws;
     if (w.prec == prec && w.m == m && w.s >= s && w.nbb >= nbb) return DSBCG_OK;
@@ -265,7 +290,6 @@ dsbcg_status ensure_ws(dsbcg_ctx* c, int m, int s, int prec, int nbb) {
     const size_t wb = prec_elem_bytes(work_prec(prec)) * ld; // work field bytes
     const size_t db = sizeof(double2) * ld;
     (void)n;
-    CKS(dmalloc(c, &w.vring, 2 * m * fb));
     CKS(dmalloc(c, &w.zw, m * fb));
     CKS(dmalloc(c, &w.y, m * fb));
     if (c->schur) {
@@ -296,9 +320,7 @@ dsbcg_status ensure_ws(dsbcg_ctx* c, int m, int s, int prec, int nbb) {
     CKS(dmalloc(c, &w.coef_a, tb));
     CKS(dmalloc(c, &w.coef_bh, tb));
     CKS(dmalloc(c, &w.coefS, tb));
-    CKS(dmalloc(c, &w.coefU, (size_t)s * tb));
-    CKS(dmalloc(c, &w.coefL, (size_t)s * tb));
-    CKS(dmalloc(c, (void**)&w.active, s * sizeof(int)));
+
     CKS(dmalloc(c, (void**)&w.conv_step, (size_t)s * m * sizeof(int)));
     CKS(dmalloc(c, (void**)&w.res, (size_t)s * m * sizeof(double)));
     CKS(dmalloc(c, (void**)&w.sigma, s * sizeof(double)));
@@ -310,6 +332,32 @@ dsbcg_status ensure_ws(dsbcg_ctx* c, int m, int s, int prec, int nbb) {
     CK(cudaMallocHost((void**)&w.h_norms, (size_t)(s + 1) * m * sizeof(double)));
     CK(cudaMallocHost((void**)&w.h_conv, (size_t)s * m * sizeof(int)));
     CK(cudaMallocHost((void**)&w.h_active, (size_t)s * sizeof(int)));
+    // the basis ring and the per-step coefficient tiles and flags of the
+    // shift-update chunks, last: a chunk that does not fit is halved, down
+    // to the per-step update with a two-block ring
+    int chunk0 = chunk_steps((size_t)m * fb, 16, 16);
+    for (;; chunk0 /= 2) {
+        void *ring = nullptr, *cu = nullptr, *cl = nullptr, *act = nullptr;
+        if (cudaMalloc(&ring, (size_t)(chunk0 + 1) * m * fb) == cudaSuccess &&
+            cudaMalloc(&cu, (size_t)chunk0 * s * tb) == cudaSuccess &&
+            cudaMalloc(&cl, (size_t)chunk0 * s * tb) == cudaSuccess &&
+            cudaMalloc(&act, (size_t)chunk0 * s * sizeof(int)) == cudaSuccess) {
+            w.vring = ring;
+            w.coefU = cu;
+            w.coefL = cl;
+            w.active = (int*)act;
+            for (void* q : {ring, cu, cl, act}) w.mem.push_back(q);
+            break;
+        }
+        cudaGetLastError();
+        for (void* q : {ring, cu, cl, act})
+            if (q) cudaFree(q);
+        if (chunk0 == 1) {
+            fprintf(stderr, "dsbcg: device allocation of the two-block basis ring (%zu bytes) failed\n",
+                    (size_t)2 * m * fb);
+            return DSBCG_ERR_OOM;
+        }
+    }
     w.m = m;
     w.s = s;
     w.prec = prec;
@@ -342,6 +390,7 @@ dsbcg_status ensure_ws(dsbcg_ctx* c, int m, int s, int prec, int nbb) {
     L0.h_ctl = w.h_ctl;
     L0.h_conv = w.h_conv;
     L0.h_active = w.h_active;
+    L0.chunk = chunk0;
     w.lanes.assign(1, L0);
     return DSBCG_OK;
 }
@@ -356,8 +405,10 @@ int ensure_refine_lanes(dsbcg_ctx* c, int want) {
     // a lane's buffers; lanes stop while a tenth of the device (at least
     // 4 GiB) would still be free, so that large lattices keep memory for the
     // caller
-    const size_t lane_bytes = (c->schur ? 5 : 4) * m * fb + 2 * m * wb + m * db + gram_partial_doubles(M_MAX) * sizeof(double) +
-                              small_state_bytes(1) + 6 * tb;
+    const int chunk = chunk_steps((size_t)m * fb, 4, 64);
+    const size_t lane_bytes = (c->schur ? 3 : 2) * m * fb + (size_t)(chunk + 1) * m * fb + 2 * m * wb + m * db +
+                              gram_partial_doubles(M_MAX) * sizeof(double) + small_state_bytes(1) +
+                              (4 + 2 * (size_t)chunk) * tb;
     while ((int)w.lanes.size() < want) {
         size_t fr = 0, tot = 0;
         if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
@@ -367,7 +418,8 @@ int ensure_refine_lanes(dsbcg_ctx* c, int want) {
         const size_t reserve = std::max(tot / 10, (size_t)4 << 30);
         if (fr < lane_bytes + reserve) break;
         Lane L;
-        bool ok = dmalloc(c, &L.vring, 2 * m * fb) == DSBCG_OK && dmalloc(c, &L.zw, m * fb) == DSBCG_OK &&
+        L.chunk = chunk;
+        bool ok = dmalloc(c, &L.vring, (size_t)(chunk + 1) * m * fb) == DSBCG_OK && dmalloc(c, &L.zw, m * fb) == DSBCG_OK &&
                   (!c->schur || dmalloc(c, &L.eotmp, m * fb) == DSBCG_OK) &&
                   dmalloc(c, &L.y, m * fb) == DSBCG_OK && dmalloc(c, &L.P, m * wb) == DSBCG_OK &&
                   dmalloc(c, &L.Xin, m * wb) == DSBCG_OK && dmalloc(c, (void**)&L.rhs, m * db) == DSBCG_OK &&
@@ -377,8 +429,9 @@ int ensure_refine_lanes(dsbcg_ctx* c, int want) {
                   dmalloc(c, (void**)&L.G, M_MAX * M_MAX * sizeof(double2)) == DSBCG_OK &&
                   dmalloc(c, (void**)&L.diag, M_MAX * sizeof(double)) == DSBCG_OK &&
                   dmalloc(c, &L.coef_a, tb) == DSBCG_OK && dmalloc(c, &L.coef_bh, tb) == DSBCG_OK &&
-                  dmalloc(c, &L.coefS, tb) == DSBCG_OK && dmalloc(c, &L.coefU, tb) == DSBCG_OK &&
-                  dmalloc(c, &L.coefL, tb) == DSBCG_OK && dmalloc(c, (void**)&L.active, sizeof(int)) == DSBCG_OK &&
+                  dmalloc(c, &L.coefS, tb) == DSBCG_OK && dmalloc(c, &L.coefU, (size_t)chunk * tb) == DSBCG_OK &&
+                  dmalloc(c, &L.coefL, (size_t)chunk * tb) == DSBCG_OK &&
+                  dmalloc(c, (void**)&L.active, (size_t)chunk * sizeof(int)) == DSBCG_OK &&
                   dmalloc(c, (void**)&L.conv_step, m * sizeof(int)) == DSBCG_OK &&
                   dmalloc(c, (void**)&L.res, m * sizeof(double)) == DSBCG_OK &&
                   dmalloc(c, (void**)&L.sigma, sizeof(double)) == DSBCG_OK &&
@@ -638,6 +691,7 @@ dsbcg_status lane_start(dsbcg_ctx* c, Lane& L, const void* rhs, int rhs_prec, si
     L.s_in = s_in;
     L.prec = prec;
     L.step = 0;
+    L.k0 = 0;
     L.max_steps = max_steps;
     L.freeze = freeze;
     L.poll_every = poll_every;
@@ -651,12 +705,24 @@ dsbcg_status lane_enqueue(dsbcg_ctx* c, Lane& L) {
     const int prec = L.prec, wp = work_prec(prec), m_in = L.m_in, s_in = L.s_in;
     const size_t ld = c->ld, n = c->n;
     const size_t fb = prec_elem_bytes(prec) * ld;
+    const size_t cb = (wp == P64 ? 16 : 8) * (size_t)M_MAX * M_MAX;    // one coefficient tile
     cudaStream_t st = L.st;
     char* ring = (char*)L.vring;
+    const int C = L.chunk, R = C + 1;
+    auto slot = [&](int k) { return ring + (size_t)(k % R) * m_in * fb; };     // V_k
+    // P_j and X_j take the steps L.k0 + 1 .. L.step (the chunk's executed ones)
+    auto flush = [&]() {
+        if (L.step == L.k0) return;
+        Prof p(c, DSBCG_KCLASS_SHIFT, 1, st);
+        launch_shift_chunk(prec, ring, (size_t)m_in * ld, R, ld, L.P, L.Xin, ld, n, s_in, m_in, L.ctl, m_in, L.k0,
+                           C, L.coefU, L.coefL, L.active, c->hscale, st);
+        L.k0 = L.step;
+    };
     for (int q = 0; q < L.poll_every && L.step < L.max_steps; ++q) {
         const int step = ++L.step;
-        void* Vk = ring + (size_t)(step % 2) * m_in * fb;
-        void* Vo = ring + (size_t)((step + 1) % 2) * m_in * fb;     // V_{k-1}, then V_{k+1}
+        void* Vk = slot(step);
+        void* Vo = slot(step - 1);     // V_{k-1} (unused at k = 1)
+        const int hs = (step - 1) % C;                 // this step's coefficient and flag slot
         apply_op(c, prec, L.y, L.zw, Vk, L.eotmp, ld, L.ctl, 0, m_in, c->hscale, st, DSBCG_KCLASS_DSLASH);
         {
             Prof p(c, DSBCG_KCLASS_GRAM, 1, st);
@@ -680,21 +746,26 @@ dsbcg_status lane_enqueue(dsbcg_ctx* c, Lane& L) {
         {
             Prof p(c, DSBCG_KCLASS_SMALL, 1, st);
             launch_small_step(L.ss, L.ctl, L.partials, L.nblk, s_in, m_in, L.dtol, L.sigma, L.target, L.freeze, wp,
-                              L.sfp64, L.coefS, L.coefU, L.coefL, L.active, L.conv_step, L.res, st);
+                              L.sfp64, L.coefS, (char*)L.coefU + (size_t)hs * s_in * cb,
+                              (char*)L.coefL + (size_t)hs * s_in * cb, L.active + (size_t)hs * s_in, L.conv_step,
+                              L.res, st);
         }
         {
-            Prof p(c, DSBCG_KCLASS_SHIFT, 1, st);
-            launch_shift_update(prec, wp, Vo, L.zw, Vk, ld, L.P, L.Xin, ld, n, s_in, m_in, L.ctl, m_in, L.coefS,
-                                L.coefU, L.coefL, L.active, c->hscale, st);
+            Prof p(c, DSBCG_KCLASS_UPDATE, 1, st);
+            launch_v_update(prec, slot(step + 1), L.zw, ld, n, L.ctl, m_in, L.coefS, c->hscale, st);
         }
         {
             Prof p(c, DSBCG_KCLASS_SMALL, 1, st);
-            launch_small_finish(L.ss, L.ctl, s_in, m_in, L.active, st);
+            launch_small_finish(L.ss, L.ctl, s_in, m_in, L.active + (size_t)hs * s_in, st);
         }
+        if (L.step - L.k0 == C) flush();
     }
+    flush();                           // P_j, X_j current at the end of every batch
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(L.h_ctl, L.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
-    if (L.h_active) CK(cudaMemcpyAsync(L.h_active, L.active, (size_t)s_in * sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (L.h_active && L.step > 0)
+        CK(cudaMemcpyAsync(L.h_active, L.active + (size_t)((L.step - 1) % C) * s_in, (size_t)s_in * sizeof(int),
+                           cudaMemcpyDeviceToHost, st));
     return DSBCG_OK;
 }
 
@@ -744,6 +815,7 @@ dsbcg_status lane_finish(dsbcg_ctx* c, Lane& L, InnerResult* out, int step_offse
         c->kbytes[DSBCG_KCLASS_GRAM] += h.f_gram * eb;
         c->kbytes[DSBCG_KCLASS_UPDATE] += h.f_update * eb;
         c->kbytes[DSBCG_KCLASS_SHIFT] += h.f_shift_s * eb + h.f_shift_w * wbn;
+        c->kflops[DSBCG_KCLASS_SHIFT] += 8.0 * (double)h.f_shift_cmac * n;
     }
     out->steps = h.last_step;
     out->mvms = h.mvms;
@@ -820,6 +892,7 @@ dsbcg_status solve_core(dsbcg_ctx* c, int m, const void* B, int nbb, int s, cons
         c->kms[q] = 0;
         c->klaunch[q] = 0;
         c->kbytes[q] = 0;
+        c->kflops[q] = 0;
     }
 
     // --- inputs: B -> internal high-precision fields (staging through X64's storage if on the host)
@@ -1276,6 +1349,7 @@ dsbcg_status solve_core(dsbcg_ctx* c, int m, const void* B, int nbb, int s, cons
             stats->kernel_ms[q] = c->kms[q];
             stats->kernel_launches[q] = c->klaunch[q];
             stats->kernel_bytes[q] = c->kbytes[q];
+            stats->kernel_flops[q] = c->kflops[q];
         }
         stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
@@ -1444,6 +1518,7 @@ dsbcg_status dsbcg_read_profile(dsbcg_ctx* c, double kernel_ms[8], long long ker
         c->kms[q] = 0;
         c->klaunch[q] = 0;
         c->kbytes[q] = 0;
+        c->kflops[q] = 0;
     }
     return DSBCG_OK;
 }

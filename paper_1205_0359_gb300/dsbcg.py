@@ -56,7 +56,7 @@ class Stats(ctypes.Structure):
                 ("true_relres", ctypes.POINTER(ctypes.c_double)),
                 ("conv_step", ctypes.POINTER(ctypes.c_int)),
                 ("kernel_ms", ctypes.c_double * 8), ("kernel_launches", ctypes.c_longlong * 8),
-                ("kernel_bytes", ctypes.c_double * 8)]
+                ("kernel_bytes", ctypes.c_double * 8), ("kernel_flops", ctypes.c_double * 8)]
 
 
 _lib_handle = None
@@ -379,7 +379,8 @@ def _stats_dict(code, st, rel, conv):
                 final_rank=st.final_rank, seconds=st.seconds, true_relres=rel, conv_step=conv,
                 kernel_ms={KCLASS[q]: st.kernel_ms[q] for q in range(7)},
                 kernel_launches={KCLASS[q]: st.kernel_launches[q] for q in range(7)},
-                kernel_bytes={KCLASS[q]: st.kernel_bytes[q] for q in range(7)})
+                kernel_bytes={KCLASS[q]: st.kernel_bytes[q] for q in range(7)},
+                kernel_flops={KCLASS[q]: st.kernel_flops[q] for q in range(7)})
 
 
 def _as_c128(t):

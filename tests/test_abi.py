@@ -64,7 +64,7 @@ int main(void) {
     OFF(dsbcg_stats, block_steps); OFF(dsbcg_stats, mvms); OFF(dsbcg_stats, deflations);
     OFF(dsbcg_stats, restarts); OFF(dsbcg_stats, final_rank); OFF(dsbcg_stats, seconds);
     OFF(dsbcg_stats, true_relres); OFF(dsbcg_stats, conv_step); OFF(dsbcg_stats, kernel_ms);
-    OFF(dsbcg_stats, kernel_launches); OFF(dsbcg_stats, kernel_bytes);
+    OFF(dsbcg_stats, kernel_launches); OFF(dsbcg_stats, kernel_bytes); OFF(dsbcg_stats, kernel_flops);
     printf("prec fp64 %d\nprec fp32 %d\nprec bf16 %d\nprec fp16 %d\nprec df32 %d\n", DSBCG_PREC_FP64,
            DSBCG_PREC_FP32, DSBCG_PREC_BF16, DSBCG_PREC_FP16, DSBCG_PREC_DF32);
     printf("op D %d\nop Ddag %d\nop A %d\n", DSBCG_OP_D, DSBCG_OP_DDAG, DSBCG_OP_A);

@@ -27,7 +27,7 @@ pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda")
 
 
-@pytest.fixture(scope="module")
+@pytest.fixture()
 def w3():
     wl = synth.make_workload("w3_24x24x24x48")
     ctx = dsbcg.Context(wl["dims"], torch.from_numpy(wl["U"]).to(DEV), wl["kappa"])
@@ -69,6 +69,9 @@ def test_w3_precision_ladder(w3):
 
 
 def test_w5_full_size_near_dependent():
+    # the solve's workspace is about 170 GB: give back what earlier tests
+    # left in torch's cache
+    torch.cuda.empty_cache()
     wl = synth.make_workload("w5_32x32x32x64")
     ctx = dsbcg.Context(wl["dims"], torch.from_numpy(wl["U"]).to(DEV), wl["kappa"])
     try:
