@@ -760,6 +760,181 @@ void launch_ib_t(void* V1, size_t ldv, const void* B, int bprec, size_t ldb, siz
     }
 }
 
+// The same chunked update for FP32 work precision (FP32, BF16 and FP16
+// storage), on the packed FP32 pipe: each __ffma2_rn performs the FMA of one
+// complex component for two neighbouring output columns, so every element
+// sees exactly the scalar sequence of cfma / cfms (one rounding per FMA, same
+// order) at half the instruction count.  The coefficient tiles are staged as
+// {re_i, re_i+1, im_i, im_i+1} per (row a, column pair); X_j and the new P_j
+// are held as (re, re) / (im, im) column pairs.  The next step's V_{k+1} rows
+// arrive in shared memory by per-thread asynchronous copies (each thread
+// copies the elements it reads itself), one step ahead of their use.
+template <int NF, int P>
+__host__ __device__ constexpr size_t sc32_smem_bytes(int rows) {
+    return 4 * (size_t)NF * NF * sizeof(float2) + 2 * (size_t)NF * rows * sizeof(typename Tr<P>::S2);
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* dst_smem, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst_smem)), "l"(src), "n"(BYTES)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int P, int NF, int ROWS>
+__global__ void __launch_bounds__(ROWS, NF <= 12 ? 4 : 1) shift_chunk32_kernel(
+    const typename Tr<P>::S2* __restrict__ ring, size_t slot_elems, int R, size_t ld, float2* __restrict__ Pb,
+    float2* __restrict__ Xb, size_t ldw, size_t n, int s, int m, Ctl* __restrict__ ctl, int k0, int C,
+    const float2* __restrict__ cU, const float2* __restrict__ cL, const int* __restrict__ act, float hscale) {
+    static_assert(NF % 2 == 0, "column pairs");
+    constexpr int NP = NF / 2;
+    using SE = typename Tr<P>::S2;
+    const int j = (int)(blockIdx.x % (unsigned)s);
+    const int kend = min(k0 + C, ctl->last_step);
+    if (kend <= k0 || !act[(size_t)(k0 % C) * s + j]) return;
+    extern __shared__ __align__(16) unsigned char sc_smem[];
+    float* sCo = reinterpret_cast<float*>(sc_smem);                           // [2 buffers][U, L][NP][NF][4]
+    SE* sV = reinterpret_cast<SE*>(sc_smem + 4 * (size_t)NF * NF * sizeof(float2));   // [2][NF][ROWS]
+    const int tid = threadIdx.x;
+    const size_t e0 = (size_t)(blockIdx.x / (unsigned)s) * ROWS;
+    const bool ok = e0 + tid < n;
+    const size_t e = e0 + (ok ? tid : 0);
+    const float inv = (P == PBF16 || P == PF16) ? 1.f / hscale : 1.f;
+    const size_t tile = (size_t)M_MAX * M_MAX;
+    float2* Pj = Pb + (size_t)j * m * ldw;
+    float2* Xj = Xb + (size_t)j * m * ldw;
+    // rows of V_{k+1} (ring slot vs) into V buffer vb, this thread's element only
+    auto prefetch = [&](int vs, int vb) {
+        const SE* g = ring + (size_t)vs * slot_elems + e;
+        SE* d = sV + (size_t)vb * NF * ROWS + tid;
+#pragma unroll
+        for (int c = 0; c < NF; ++c)
+            if (c < m) cp_async_elem<sizeof(SE)>(d + c * ROWS, g + (size_t)c * ld);
+        cp_async_commit();
+    };
+    int mk_ = ctl->hmk[k0 & (CTL_HIST - 1)];
+    float2 t[NF];
+    float2 xr[NP], xi[NP];
+#pragma unroll
+    for (int a = 0; a < NF; ++a) {
+        if (a < mk_) {
+            if (k0 == 0) {
+                const auto q = Elem<P>::ld(ring + slot_elems + (size_t)a * ld, e, inv);     // V_1
+                t[a] = make_float2((float)q.x, (float)q.y);
+            } else {
+                t[a] = Pj[(size_t)a * ldw + e];
+            }
+        } else {
+            t[a] = make_float2(0.f, 0.f);
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        const float2 x0 = 2 * p < m ? Xj[(size_t)(2 * p) * ldw + e] : make_float2(0.f, 0.f);
+        const float2 x1 = 2 * p + 1 < m ? Xj[(size_t)(2 * p + 1) * ldw + e] : make_float2(0.f, 0.f);
+        xr[p] = make_float2(x0.x, x1.x);
+        xi[p] = make_float2(x0.y, x1.y);
+    }
+    int q = k0 % C;                    // coefficient / flag slot of step k
+    int vs = (k0 + 2) % R;             // ring slot of V_{k+1}
+    prefetch(vs, 0);
+    int mn = mk_;
+    for (int k = k0 + 1; k <= kend; ++k) {
+        if (!act[(size_t)q * s + j]) break;
+        mn = ctl->hmn[(k - 1) & (CTL_HIST - 1)];
+        const int b = (k - k0 - 1) & 1;
+        const int vs_next = vs + 1 == R ? 0 : vs + 1;
+        const bool ahead = k < kend;
+        if (ahead) prefetch(vs_next, b ^ 1);
+        // this step's tiles into buffer b (its previous readers, step k - 2,
+        // are past the barrier of step k - 1)
+        float* bU = sCo + (size_t)b * 2 * NF * NF * 2;
+        float* bL = bU + NF * NF * 2;
+        const float2* gU = cU + ((size_t)q * s + j) * tile;
+        const float2* gL = cL + ((size_t)q * s + j) * tile;
+        for (int u = tid; u < NF * NF; u += ROWS) {
+            const int a = u / NF, i = u % NF;
+            const int at = (a * NP + (i >> 1)) * 4 + (i & 1);
+            const float2 cu = gU[a * M_MAX + i], cl = gL[a * M_MAX + i];
+            bU[at] = cu.x;
+            bU[at + 2] = cu.y;
+            bL[at] = cl.x;
+            bL[at + 2] = cl.y;
+        }
+        __syncthreads();
+        // X_j += P_j Ut_j
+#pragma unroll
+        for (int a = 0; a < NF; ++a) {
+            const float2 tr = make_float2(t[a].x, t[a].x), ti = make_float2(t[a].y, t[a].y);
+            const float2 nti = make_float2(-t[a].y, -t[a].y);
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const float4 u = *reinterpret_cast<const float4*>(&bU[(a * NP + p) * 4]);
+                const float2 ure = make_float2(u.x, u.y), uim = make_float2(u.z, u.w);
+                xr[p] = __ffma2_rn(tr, ure, xr[p]);
+                xr[p] = __ffma2_rn(nti, uim, xr[p]);
+                xi[p] = __ffma2_rn(tr, uim, xi[p]);
+                xi[p] = __ffma2_rn(ti, ure, xi[p]);
+            }
+        }
+        // P_j <- V_{k+1} - P_j Lh_j
+        if (ahead) cp_async_wait<1>();
+        else cp_async_wait<0>();
+        const SE* v = sV + (size_t)b * NF * ROWS + tid;
+        float2 pr[NP], pi[NP];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            float2 v0 = make_float2(0.f, 0.f), v1 = make_float2(0.f, 0.f);
+            if (2 * p < mn) {
+                const auto w = Elem<P>::ld(v, (size_t)(2 * p) * ROWS, inv);
+                v0 = make_float2((float)w.x, (float)w.y);
+            }
+            if (2 * p + 1 < mn) {
+                const auto w = Elem<P>::ld(v, (size_t)(2 * p + 1) * ROWS, inv);
+                v1 = make_float2((float)w.x, (float)w.y);
+            }
+            pr[p] = make_float2(v0.x, v1.x);
+            pi[p] = make_float2(v0.y, v1.y);
+        }
+#pragma unroll
+        for (int a = 0; a < NF; ++a) {
+            const float2 ntr = make_float2(-t[a].x, -t[a].x), ti = make_float2(t[a].y, t[a].y);
+            const float2 nti = make_float2(-t[a].y, -t[a].y);
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                const float4 l = *reinterpret_cast<const float4*>(&bL[(a * NP + p) * 4]);
+                const float2 lre = make_float2(l.x, l.y), lim = make_float2(l.z, l.w);
+                pr[p] = __ffma2_rn(ntr, lre, pr[p]);
+                pr[p] = __ffma2_rn(ti, lim, pr[p]);
+                pi[p] = __ffma2_rn(ntr, lim, pi[p]);
+                pi[p] = __ffma2_rn(nti, lre, pi[p]);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            t[2 * p] = 2 * p < mn ? make_float2(pr[p].x, pi[p].x) : make_float2(0.f, 0.f);
+            t[2 * p + 1] = 2 * p + 1 < mn ? make_float2(pr[p].y, pi[p].y) : make_float2(0.f, 0.f);
+        }
+        q = q + 1 == C ? 0 : q + 1;
+        vs = vs_next;
+    }
+    cp_async_wait<0>();                 // no copy in flight when the CTA leaves
+    if (ok) {
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            if (2 * p < m) Xj[(size_t)(2 * p) * ldw + e] = make_float2(xr[p].x, xi[p].x);
+            if (2 * p + 1 < m) Xj[(size_t)(2 * p + 1) * ldw + e] = make_float2(xr[p].y, xi[p].y);
+        }
+#pragma unroll
+        for (int c = 0; c < NF; ++c)
+            if (c < mn) Pj[(size_t)c * ldw + e] = t[c];
+    }
+    if (blockIdx.x < (unsigned)s && tid == 0)
+        atomicAdd(reinterpret_cast<unsigned long long*>(&ctl->f_shift_w), (unsigned long long)(mk_ + 2 * m + mn));
+}
+
 template <int P>
 void launch_vu_t(void* Vnext, const void* W, size_t ld, size_t n, const Ctl* ctl, int nf_max, const void* coefS,
                  float hscale, cudaStream_t st) {
@@ -784,14 +959,22 @@ void launch_sc_t(const void* ring, size_t slot_elems, int R, size_t ld, void* Pp
 #define BI_SC(NF)                                                                                           \
     {                                                                                                       \
         constexpr int ROWS = 128;                                                                           \
-        constexpr size_t SMEM = sc_smem_bytes<NF, PW>();                                                    \
-        static std::atomic<unsigned long long> devs{0};                                                     \
-        max_dyn_smem_once(shift_chunk_kernel<P, PW, NF, ROWS>, (int)SMEM, devs);                            \
         const unsigned g = (unsigned)(((n + ROWS - 1) / ROWS) * (size_t)s);                                 \
-        shift_chunk_kernel<P, PW, NF, ROWS><<<g, ROWS, SMEM, st>>>((const S2*)ring, slot_elems, R, ld, (W2*)Pp, \
-                                                                   (W2*)X, ldw, n, s, m, ctl, k0, C,        \
-                                                                   (const CW*)coefU, (const CW*)coefL, active, \
-                                                                   hscale);                                 \
+        if constexpr (PW == P64) {                                                                          \
+            constexpr size_t SMEM = sc_smem_bytes<NF, PW>();                                                \
+            static std::atomic<unsigned long long> devs{0};                                                 \
+            max_dyn_smem_once(shift_chunk_kernel<P, PW, NF, ROWS>, (int)SMEM, devs);                        \
+            shift_chunk_kernel<P, PW, NF, ROWS><<<g, ROWS, SMEM, st>>>(                                      \
+                (const S2*)ring, slot_elems, R, ld, (W2*)Pp, (W2*)X, ldw, n, s, m, ctl, k0, C,              \
+                (const CW*)coefU, (const CW*)coefL, active, hscale);                                        \
+        } else {                                                                                            \
+            constexpr size_t SMEM = sc32_smem_bytes<NF, P>(ROWS);                                           \
+            static std::atomic<unsigned long long> devs{0};                                                 \
+            max_dyn_smem_once(shift_chunk32_kernel<P, NF, ROWS>, (int)SMEM, devs);                          \
+            shift_chunk32_kernel<P, NF, ROWS><<<g, ROWS, SMEM, st>>>(                                        \
+                (const S2*)ring, slot_elems, R, ld, (float2*)Pp, (float2*)X, ldw, n, s, m, ctl, k0, C,      \
+                (const float2*)coefU, (const float2*)coefL, active, hscale);                                \
+        }                                                                                                   \
     }
     BI_DISPATCH_NF(nf_max, BI_SC)
 #undef BI_SC
