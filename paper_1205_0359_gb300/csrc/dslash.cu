@@ -228,14 +228,17 @@ __global__ void __launch_bounds__(32, (P == PDD || P == P64) ? 12 : 24) dslash_k
         if (ctl->done) return;
         nf = ctl->mk;
     }
-    // 1D grid: block b covers field b % nfg of site tile b / nfg (fields fastest)
-    const int f = (int)(blockIdx.x % (unsigned)nfg);
-    if (f >= nf) return;
+    // 1D work index: block b covers field b % nfg of site tile b / nfg
+    // (fields fastest); a grid smaller than the work strides over it
+    const unsigned nwork = (unsigned)nfg * (unsigned)((g.V + 31) / 32);
+    for (unsigned blk = blockIdx.x; blk < nwork; blk += gridDim.x) {
+    const int f = (int)(blk % (unsigned)nfg);
+    if (f >= nf) continue;
     const int tx = threadIdx.x;
-    const int site0 = (int)(blockIdx.x / (unsigned)nfg) * 32;
+    const int site0 = (int)(blk / (unsigned)nfg) * 32;
     const size_t V = (size_t)g.V;
     const int x = site0 + tx;
-    if (x >= g.V) return;
+    if (x >= g.V) continue;
     R inv = R(1), scl = R(1);
     if constexpr (P == PBF16 || P == PF16) {
         inv = R(1) / R(hscale);
@@ -326,6 +329,7 @@ __global__ void __launch_bounds__(32, (P == PDD || P == P64) ? 12 : 24) dslash_k
             }
         }
         SpinorIO<P>::store(out + (size_t)f * ld, V, (size_t)x, p, scl, plo);
+    }
     }
 }
 
@@ -635,7 +639,7 @@ __global__ void __launch_bounds__(32, (P == PDD || P == P64) ? 12 : 24) dslash_h
 
 void launch_dslash(int prec, void* out, const void* in, size_t ld, const void* links, const Geom& g,
                    double kappa, int dag, const Ctl* ctl, int nf_static, int nf_max, float hscale,
-                   cudaStream_t st, const void* links12) {
+                   cudaStream_t st, const void* links12, int max_ctas) {
     // D^H = gamma_5 D gamma_5: gamma_5 on the input and on the output
     const int g5in = dag, g5out = dag;
     // one CTA per (field, 32-site tile); with a control block the width is
@@ -644,6 +648,10 @@ void launch_dslash(int prec, void* out, const void* in, size_t ld, const void* l
     const int nf_grid = nfg < 1 ? 1 : nfg;
     dim3 block(32);
     dim3 grid((unsigned)(nf_grid * ((g.V + 31) / 32)));
+    // FP64 / double-float: at most max_ctas CTAs striding over the work, so
+    // that an ALU-bound stencil on a side stream leaves the SMs room for the
+    // kernels of other streams
+    if (max_ctas > 0 && grid.x > (unsigned)max_ctas) grid.x = (unsigned)max_ctas;
     const size_t sm = 0;
     // FP32 and 16-bit fields: CTAs of 32 sites x CTA_FIELDS fields with the
     // tile's links staged in shared memory

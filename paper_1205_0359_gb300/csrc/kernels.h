@@ -73,7 +73,7 @@ void launch_dot_re_blocks(const double2* a, const double2* b, int s, size_t cnt,
 void launch_dslash(int prec, void* out, const void* in, size_t ld, const void* links,
                    const Geom& g, double kappa, int dag, const Ctl* ctl,
                    int nf_static, int nf_max, float hscale, cudaStream_t st,
-                   const void* links12 = nullptr);
+                   const void* links12 = nullptr, int max_ctas = 0);
 
 // Half-lattice hopping term of the even-odd operator (every extent even; half
 // fields of V / 2 sites, half index = canonical site / 2):

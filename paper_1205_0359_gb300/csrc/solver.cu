@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <chrono>
 #include <deque>
+#include <cstdlib>
 #include <functional>
 #include <mutex>
 #include <thread>
@@ -114,6 +115,9 @@ struct dsbcg_ctx {
     // context's stream, and the events that order the two; created on first use
     cudaStream_t rst = nullptr;
     cudaEvent_t ev_joint = nullptr, ev_ref = nullptr;
+    // CTAs of an FP64 true-residual stencil launch (0: one per work item);
+    // set on first use
+    int resid_ctas = -1;
     int debug_first_wait = -1;           // test hook of the block Gram kernel (dsbcg_debug_first_wait)
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -561,6 +565,28 @@ void apply_dhat(dsbcg_ctx* c, int p, void* out, const void* in, void* tmp, size_
 // A = D^H D (two stencils; mid receives D in) or, on a context with the Schur
 // operator, Ahat = Dhat^H Dhat (four half-lattice passes; mid receives
 // Dhat in, tmp is scratch for even-parity half fields)
+// CTAs of the FP64 true-residual stencil: a few per SM.  The stencil is
+// bound by the FP64 pipe (2 FMA per clock per SM on GB300), which a few
+// warps per SM keep busy, so a capped grid striding over the work leaves the
+// rest of each SM to the FP32 kernels of the solve's other streams
+// (DSBCG_RESIDUAL_CTAS_PER_SM overrides the default of 8; 0 lifts the cap).  At
+// 16^3 x 32 with 12 fields the stencil alone takes 130 ms per solve at 8, 134
+// at 4 and 253 at 2 CTAs per SM (127 uncapped): below 8 warps per SM its
+// neighbour loads are no longer hidden.
+int residual_ctas(dsbcg_ctx* c) {
+    if (c->resid_ctas < 0) {
+        int per_sm = 8, dev = 0, sms = 0;
+        if (const char* e = getenv("DSBCG_RESIDUAL_CTAS_PER_SM")) per_sm = std::max(0, atoi(e));
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            sms = 0;
+        }
+        c->resid_ctas = per_sm * sms;
+    }
+    return c->resid_ctas;
+}
+
 void apply_op(dsbcg_ctx* c, int p, void* out, void* mid, const void* in, void* tmp, size_t ld, const Ctl* ctl,
               int nf_static, int nf_max, float hs, cudaStream_t st, int cls) {
     if (c->schur) {
@@ -568,13 +594,16 @@ void apply_op(dsbcg_ctx* c, int p, void* out, void* mid, const void* in, void* t
         apply_dhat(c, p, out, mid, tmp, ld, 1, ctl, nf_static, nf_max, hs, st, cls);
         return;
     }
+    const int cap = (cls == DSBCG_KCLASS_RESIDUAL && p == P64) ? residual_ctas(c) : 0;
     {
         Prof q(c, cls, 1, st);
-        launch_dslash(p, mid, in, ld, c->links[p], c->g, c->kappa, 0, ctl, nf_static, nf_max, hs, st, c->links12[p]);
+        launch_dslash(p, mid, in, ld, c->links[p], c->g, c->kappa, 0, ctl, nf_static, nf_max, hs, st, c->links12[p],
+                      cap);
     }
     {
         Prof q(c, cls, 1, st);
-        launch_dslash(p, out, mid, ld, c->links[p], c->g, c->kappa, 1, ctl, nf_static, nf_max, hs, st, c->links12[p]);
+        launch_dslash(p, out, mid, ld, c->links[p], c->g, c->kappa, 1, ctl, nf_static, nf_max, hs, st, c->links12[p],
+                      cap);
     }
 }
 
