@@ -561,18 +561,14 @@ void apply_dhat(dsbcg_ctx* c, int p, void* out, const void* in, void* tmp, size_
     }
 }
 
-// out = Op in for the fields of a block in precision p: the normal operator
-// A = D^H D (two stencils; mid receives D in) or, on a context with the Schur
-// operator, Ahat = Dhat^H Dhat (four half-lattice passes; mid receives
-// Dhat in, tmp is scratch for even-parity half fields)
-// CTAs of the FP64 true-residual stencil: a few per SM.  The stencil is
-// bound by the FP64 pipe (2 FMA per clock per SM on GB300), which a few
-// warps per SM keep busy, so a capped grid striding over the work leaves the
-// rest of each SM to the FP32 kernels of the solve's other streams
-// (DSBCG_RESIDUAL_CTAS_PER_SM overrides the default of 8; 0 lifts the cap).  At
-// 16^3 x 32 with 12 fields the stencil alone takes 130 ms per solve at 8, 134
-// at 4 and 253 at 2 CTAs per SM (127 uncapped): below 8 warps per SM its
-// neighbour loads are no longer hidden.
+// CTAs of the FP64 true-residual stencil.  The stencil is bound by the FP64
+// pipe (2 FMA per clock per SM on GB300) and the latency of its neighbour
+// loads; eight one-warp CTAs per SM keep it at full speed, so a grid of 8
+// CTAs per SM striding over the work leaves the rest of each SM to the FP32
+// kernels of the solve's other streams (DSBCG_RESIDUAL_CTAS_PER_SM overrides
+// the 8; 0 lifts the cap).  At 16^3 x 32 with 12 fields the residual stencils
+// of one solve take 130 ms at 8, 134 at 4 and 253 at 2 CTAs per SM (127
+// uncapped), and the solve 353 ms at 8 against 364 uncapped.
 int residual_ctas(dsbcg_ctx* c) {
     if (c->resid_ctas < 0) {
         int per_sm = 8, dev = 0, sms = 0;
@@ -587,6 +583,10 @@ int residual_ctas(dsbcg_ctx* c) {
     return c->resid_ctas;
 }
 
+// out = Op in for the fields of a block in precision p: the normal operator
+// A = D^H D (two stencils; mid receives D in) or, on a context with the Schur
+// operator, Ahat = Dhat^H Dhat (four half-lattice passes; mid receives
+// Dhat in, tmp is scratch for even-parity half fields)
 void apply_op(dsbcg_ctx* c, int p, void* out, void* mid, const void* in, void* tmp, size_t ld, const Ctl* ctl,
               int nf_static, int nf_max, float hs, cudaStream_t st, int cls) {
     if (c->schur) {
