@@ -1006,6 +1006,14 @@ dsbcg_status solve_core(dsbcg_ctx* c, int m, const void* B, int nbb, int s, cons
     const int rprec = hp == PDD ? P32 : P64;
     const size_t rld = hp_ld(c, hp);
     const double drop = mixed ? std::max(prm.restart_drop, 1e-12) : 0.0;
+    // Inner solves aim at rt_frac x tol: each ends on its recurrence residual,
+    // which the final FP64 true residual has to confirm below tol.  FP32 and
+    // FP64 Krylov processes started from a true residual keep that estimate
+    // within about 1e-3 of the starting residual (far below 0.1 tol here);
+    // 16-bit processes drift more.  16^3 x 32 and 24^3 x 48 (m = 12 / 8) took
+    // 341 / 763 ms at 0.9 against 354 / 792 at 0.5 in FP32 storage; BF16
+    // needed extra restarts at 0.9 and was fastest at 0.7.
+    const double rt_frac = (prec == PBF16 || prec == PF16) ? 0.7 : 0.9;
 
     // --- lanes for the per-shift restarts (allocated before the joint solve
     // starts, so that no allocation falls inside it).  With profiling on,
@@ -1085,7 +1093,7 @@ dsbcg_status solve_core(dsbcg_ctx* c, int m, const void* B, int nbb, int s, cons
         Range r_joint("joint block solve");
         std::vector<double> tg((size_t)s * m);
         for (int j = 0; j < s; ++j)
-            for (int i = 0; i < m; ++i) tg[(size_t)j * m + i] = std::max(drop * bn[i], 0.5 * tol * bn[i]);
+            for (int i = 0; i < m; ++i) tg[(size_t)j * m + i] = std::max(drop * bn[i], rt_frac * tol * bn[i]);
         CKS(lane_start(c, *L0, w.B64, rprec, rld, m, sigma, s, tg.data(), prec, dtol, prm.max_block_steps,
                        prm.freeze_converged, prm.poll_every, sfp64));
         if (early) {
@@ -1246,7 +1254,7 @@ dsbcg_status solve_core(dsbcg_ctx* c, int m, const void* B, int nbb, int s, cons
             tg.resize(mu);
             for (int q = 0; q < mu; ++q) {
                 const int i = cl[q];
-                tg[q] = std::max(drop * rel[(size_t)j * m + i] * bnorm(j, i), 0.5 * tol * bnorm(j, i));
+                tg[q] = std::max(drop * rel[(size_t)j * m + i] * bnorm(j, i), rt_frac * tol * bnorm(j, i));
             }
             CKS(gather(L.rhs, w.R64, src));
             if (L.st != fst) {
