@@ -59,6 +59,8 @@ void launch_gram_reduce(const double* partials, int nblk, int nf_max, int herm, 
 #define EXTERN_P(P)                                                                                      \
     extern template void launch_bu_t<P>(void*, const void*, const void*, const void*, size_t, size_t, const Ctl*, \
                                         int, const void*, const void*, float, cudaStream_t);                 \
+    extern template void launch_ug_t<P>(void*, const void*, const void*, const void*, size_t, size_t, const Ctl*, \
+                                        int, const void*, const void*, double*, int, float, cudaStream_t);   \
     extern template void launch_ib_t<P>(void*, size_t, const void*, int, size_t, size_t, const double2*, int, \
                                         const Ctl*, int, float, cudaStream_t);                               \
     extern template void launch_vu_t<P>(void*, const void*, size_t, size_t, const Ctl*, int, const void*,     \
@@ -83,6 +85,21 @@ void launch_block_update(int prec, void* W, const void* Y, const void* Vk, const
         case PBF16: launch_bu_t<PBF16>(W, Y, Vk, Vp, ld, n, ctl, nf_max, coef_a, coef_bh, hscale, st); break;
         case PF16: launch_bu_t<PF16>(W, Y, Vk, Vp, ld, n, ctl, nf_max, coef_a, coef_bh, hscale, st); break;
     }
+}
+
+bool update_gram_fits(int prec, int nf_max) { return prec != P64 && nf_max <= UG_NF_MAX; }
+
+void launch_update_gram(int prec, void* W, const void* Y, const void* Vk, const void* Vp, size_t ld, size_t n,
+                        const Ctl* ctl, int nf_max, const void* coef_a, const void* coef_bh, double* partials,
+                        int nblk, float hscale, cudaStream_t st) {
+#define UG_ARGS W, Y, Vk, Vp, ld, n, ctl, nf_max, coef_a, coef_bh, partials, nblk, hscale, st
+    switch (prec) {
+        case P64: launch_ug_t<P64>(UG_ARGS); break;
+        case P32: launch_ug_t<P32>(UG_ARGS); break;
+        case PBF16: launch_ug_t<PBF16>(UG_ARGS); break;
+        case PF16: launch_ug_t<PF16>(UG_ARGS); break;
+    }
+#undef UG_ARGS
 }
 
 void launch_init_basis(int prec, void* V1, size_t ldv, const void* B, int bprec, size_t ldb, size_t n,

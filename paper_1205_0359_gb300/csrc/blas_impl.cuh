@@ -222,6 +222,128 @@ __global__ void __launch_bounds__(256) block_update_kernel(typename Tr<P>::S2* _
     }
 }
 
+// Block update fused with the Gram W^H W of its result, for block widths up
+// to 12.  The grid (the Gram's nblk CTAs of UG_ROWS threads) strides over
+// tiles of UG_ROWS rows.  Per tile every thread first forms W for its row
+// exactly as block_update_kernel does and stores it to global memory and, in
+// the storage precision (the values a separate Gram launch would read), to
+// shared memory.  After a barrier, warp w accumulates the upper 4 x 4 tile w
+// of W^H W over the tile's rows, lanes striding the rows, in the Gram
+// kernel's operation order.  At the end each tile's warp writes its fixed-
+// order warp reduction to the partials in the Gram kernel's layout, so the
+// QR kernel that follows reads them unchanged.  W therefore crosses HBM once
+// per step instead of twice, and the step has one launch less.
+constexpr int UG_ROWS = 256;
+constexpr int UG_NF_MAX = 12;          // upper tiles (6 at width 12) <= warps (8)
+
+template <int P, int NF>
+__global__ void __launch_bounds__(UG_ROWS, 2) update_gram_kernel(
+    typename Tr<P>::S2* __restrict__ W, const typename Tr<P>::S2* __restrict__ Y,
+    const typename Tr<P>::S2* __restrict__ Vk, const typename Tr<P>::S2* __restrict__ Vp, size_t ld, size_t n,
+    const Ctl* __restrict__ ctl, int nf_max, const typename Tr<P>::C* __restrict__ ca,
+    const typename Tr<P>::C* __restrict__ cbh, double* __restrict__ partials, float hscale) {
+    static_assert(NF <= UG_NF_MAX, "fused update and Gram: widths up to 12");
+    using C = typename Tr<P>::C;
+    using R = typename Tr<P>::R;
+    using SE = typename Tr<P>::S2;
+    if (ctl->done) return;
+    const int mk_ = ctl->mk, mp = (ctl->k > 1) ? ctl->mprev : 0;
+    __shared__ C sa[NF * NF], sb[NF * NF];
+    extern __shared__ __align__(16) unsigned char ug_smem[];
+    SE* sW = reinterpret_cast<SE*>(ug_smem);                // [NF][UG_ROWS]
+    for (int t = threadIdx.x; t < NF * NF; t += blockDim.x) {
+        const int a = t / NF, b = t % NF;
+        sa[t] = ca[a * M_MAX + b];
+        sb[t] = cbh[a * M_MAX + b];
+    }
+    const R inv = (P == PBF16 || P == PF16) ? R(1) / R(hscale) : R(1);
+    const R scl = (P == PBF16 || P == PF16) ? R(hscale) : R(1);
+    const int T = (nf_max + 3) / 4;
+    const int ntl = T * (T + 1) / 2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int ti = 0, tj = 0;
+    if (warp < ntl) tile_coords(warp, T, 1, &ti, &tj);
+    const int i0 = ti * 4, j0 = tj * 4;
+    const int ni = max(0, min(4, mk_ - i0)), nj = max(0, min(4, mk_ - j0));
+    C acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = mk(R(0), R(0));
+    __syncthreads();
+    const size_t ntr = (n + UG_ROWS - 1) / UG_ROWS;
+    for (size_t q = blockIdx.x; q < ntr; q += gridDim.x) {
+        const size_t e = q * UG_ROWS + threadIdx.x;
+        if (e < n) {
+            // every operand of the row is loaded before any arithmetic
+            C v[NF], vp[NF], y[NF];
+#pragma unroll
+            for (int a = 0; a < NF; ++a) {
+                v[a] = a < mk_ ? Elem<P>::ld(Vk + (size_t)a * ld, e, inv) : mk(R(0), R(0));
+                vp[a] = a < mp ? Elem<P>::ld(Vp + (size_t)a * ld, e, inv) : mk(R(0), R(0));
+                y[a] = a < mk_ ? Elem<P>::ld(Y + (size_t)a * ld, e, inv) : mk(R(0), R(0));
+            }
+#pragma unroll
+            for (int b = 0; b < NF; ++b) {
+                if (b < mk_) {
+                    C w = y[b];
+#pragma unroll
+                    for (int a = 0; a < NF; ++a) {
+                        cfms(w, v[a], sa[a * NF + b]);
+                        cfms(w, vp[a], sb[a * NF + b]);
+                    }
+                    Elem<P>::st(W + (size_t)b * ld, e, w, scl);
+                    Elem<P>::st(sW, (size_t)b * UG_ROWS + threadIdx.x, w, scl);
+                }
+            }
+        }
+        __syncthreads();
+        if (warp < ntl && ni > 0 && nj > 0) {
+            const int rows = (int)((n - q * UG_ROWS) < (size_t)UG_ROWS ? (n - q * UG_ROWS) : (size_t)UG_ROWS);
+            for (int r = lane; r < rows; r += 32) {
+                C x[4], yv[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    x[a] = a < ni ? Elem<P>::ld(sW, (size_t)(i0 + a) * UG_ROWS + r, inv) : mk(R(0), R(0));
+                    yv[a] = a < nj ? Elem<P>::ld(sW, (size_t)(j0 + a) * UG_ROWS + r, inv) : mk(R(0), R(0));
+                }
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) cfmac(acc[a][c], x[a], yv[c]);
+            }
+        }
+        __syncthreads();
+    }
+    if (warp < ntl) {
+        // fixed-order warp reduction of the 36 slots (no diagonal norms), one write per slot
+        R v[GSLOTS];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                v[2 * (a * 4 + c)] = acc[a][c].x;
+                v[2 * (a * 4 + c) + 1] = acc[a][c].y;
+            }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[32 + c] = R(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int qq = 0; qq < GSLOTS; ++qq) v[qq] += __shfl_down_sync(0xffffffffu, v[qq], o);
+        if (lane == 0) {
+            const size_t base = ((size_t)warp * gridDim.x + blockIdx.x) * GSLOTS;
+#pragma unroll
+            for (int qq = 0; qq < GSLOTS; ++qq) {
+                if constexpr (P == P64)
+                    partials[base + qq] = (double)v[qq];
+                else
+                    reinterpret_cast<float*>(partials)[base + qq] = (float)v[qq];
+            }
+        }
+    }
+}
+
 // V1 = B S: B FP64 (nf_in fields), S FP64 M_MAX x M_MAX, V1 storage precision (ctl->mk fields)
 template <int P, int NF, int PIN>
 __global__ void __launch_bounds__(256) init_basis_kernel(typename Tr<P>::S2* __restrict__ V1, size_t ldv,
@@ -740,6 +862,29 @@ void launch_bu_t(void* W, const void* Y, const void* Vk, const void* Vp, size_t 
 }
 
 template <int P>
+void launch_ug_t(void* W, const void* Y, const void* Vk, const void* Vp, size_t ld, size_t n, const Ctl* ctl,
+                 int nf_max, const void* coef_a, const void* coef_bh, double* partials, int nblk, float hscale,
+                 cudaStream_t st) {
+    using S2 = typename Tr<P>::S2;
+    using C = typename Tr<P>::C;
+#define BI_UG(NF)                                                                                            \
+    {                                                                                                        \
+        constexpr int SMEM = NF * UG_ROWS * (int)sizeof(S2);                                                 \
+        static std::atomic<unsigned long long> devs{0};                                                      \
+        max_dyn_smem_once(update_gram_kernel<P, NF>, SMEM, devs);                                            \
+        update_gram_kernel<P, NF><<<nblk, UG_ROWS, SMEM, st>>>((S2*)W, (const S2*)Y, (const S2*)Vk,            \
+                                                               (const S2*)Vp, ld, n, ctl, nf_max, (const C*)coef_a, \
+                                                               (const C*)coef_bh, partials, hscale);          \
+    }
+    switch (nf_bucket(nf_max)) {
+        case 4: BI_UG(4); break;
+        case 8: BI_UG(8); break;
+        default: BI_UG(12); break;
+    }
+#undef BI_UG
+}
+
+template <int P>
 void launch_ib_t(void* V1, size_t ldv, const void* B, int bprec, size_t ldb, size_t n, const double2* S, int s_dd,
                  const Ctl* ctl, int nf_in, float hscale, cudaStream_t st) {
     using S2 = typename Tr<P>::S2;
@@ -983,6 +1128,8 @@ void launch_sc_t(const void* ring, size_t slot_elems, int R, size_t ld, void* Pp
 #define BI_INSTANTIATE(P)                                                                                  \
     template void launch_bu_t<P>(void*, const void*, const void*, const void*, size_t, size_t, const Ctl*, int, \
                                  const void*, const void*, float, cudaStream_t);                          \
+    template void launch_ug_t<P>(void*, const void*, const void*, const void*, size_t, size_t, const Ctl*, int, \
+                                 const void*, const void*, double*, int, float, cudaStream_t);            \
     template void launch_ib_t<P>(void*, size_t, const void*, int, size_t, size_t, const double2*, int,       \
                                  const Ctl*, int, float, cudaStream_t);                                    \
     template void launch_vu_t<P>(void*, const void*, size_t, size_t, const Ctl*, int, const void*, float,    \

@@ -104,6 +104,14 @@ void launch_gram_reduce(const double* partials, int nblk, int nf_max, int herm, 
 void launch_block_update(int prec, void* W, const void* Y, const void* Vk, const void* Vp,
                          size_t ld, size_t n, const Ctl* ctl, int nf_max,
                          const void* coef_a, const void* coef_bh, float hscale, cudaStream_t st);
+// Block update fused with the Gram of its result: W as launch_block_update,
+// and W^H W (hermitian, upper 4 x 4 tiles, no diagonal norms) as partials of
+// nblk blocks in the Gram kernel's layout.  Reduced storages and block widths
+// up to 12 (update_gram_fits); nblk is the Gram's block count for nf_max.
+bool update_gram_fits(int prec, int nf_max);
+void launch_update_gram(int prec, void* W, const void* Y, const void* Vk, const void* Vp, size_t ld, size_t n,
+                        const Ctl* ctl, int nf_max, const void* coef_a, const void* coef_bh, double* partials,
+                        int nblk, float hscale, cudaStream_t st);
 // V1 = B S (B in precision bprec: FP64, or FP32 for reduced storage;
 // storage-precision V1), S from the device m x m state (M_MAX x M_MAX, FP64,
 // or double-float when s_dd)

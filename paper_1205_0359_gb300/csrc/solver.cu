@@ -764,13 +764,21 @@ dsbcg_status lane_enqueue(dsbcg_ctx* c, Lane& L) {
             Prof p(c, DSBCG_KCLASS_SMALL, 1, st);
             launch_small_alpha(L.ss, L.ctl, L.partials, L.nblk, m_in, wp, L.sfp64, L.coef_a, L.coef_bh, st);
         }
-        {
+        if (update_gram_fits(prec, m_in)) {
+            // W and its Gram W^H W in one pass over the rows
             Prof p(c, DSBCG_KCLASS_UPDATE, 1, st);
-            launch_block_update(prec, L.zw, L.y, Vk, Vo, ld, n, L.ctl, m_in, L.coef_a, L.coef_bh, c->hscale, st);
-        }
-        {
-            Prof p(c, DSBCG_KCLASS_GRAM, 1, st);
-            launch_gram(prec, L.zw, L.zw, ld, n, L.ctl, 0, m_in, 1, 0, L.partials, L.nblk, c->hscale, st);
+            launch_update_gram(prec, L.zw, L.y, Vk, Vo, ld, n, L.ctl, m_in, L.coef_a, L.coef_bh, L.partials, L.nblk,
+                               c->hscale, st);
+        } else {
+            {
+                Prof p(c, DSBCG_KCLASS_UPDATE, 1, st);
+                launch_block_update(prec, L.zw, L.y, Vk, Vo, ld, n, L.ctl, m_in, L.coef_a, L.coef_bh, c->hscale,
+                                    st);
+            }
+            {
+                Prof p(c, DSBCG_KCLASS_GRAM, 1, st);
+                launch_gram(prec, L.zw, L.zw, ld, n, L.ctl, 0, m_in, 1, 0, L.partials, L.nblk, c->hscale, st);
+            }
         }
         {
             Prof p(c, DSBCG_KCLASS_SMALL, 1, st);
@@ -841,7 +849,9 @@ dsbcg_status lane_finish(dsbcg_ctx* c, Lane& L, InnerResult* out, int step_offse
         // the Schur operator's four passes move 10 half fields per block
         // column (the counter counts the normal operator's 4)
         c->kbytes[DSBCG_KCLASS_DSLASH] += h.f_dslash * eb * (c->schur ? 2.5 : 1.0) + link_passes(c) * h.last_step * links;
-        c->kbytes[DSBCG_KCLASS_GRAM] += h.f_gram * eb;
+        // f_gram counts V_k and Y for alpha and W for W^H W (3 m_k per step);
+        // the fused update reads W once, for both
+        c->kbytes[DSBCG_KCLASS_GRAM] += h.f_gram * eb * (update_gram_fits(prec, m_in) ? 2.0 / 3.0 : 1.0);
         c->kbytes[DSBCG_KCLASS_UPDATE] += h.f_update * eb;
         c->kbytes[DSBCG_KCLASS_SHIFT] += h.f_shift_s * eb + h.f_shift_w * wbn;
         c->kflops[DSBCG_KCLASS_SHIFT] += 8.0 * (double)h.f_shift_cmac * n;
