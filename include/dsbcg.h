@@ -331,6 +331,15 @@ dsbcg_status dsbcg_force(dsbcg_ctx* ctx, int m, int s, const void* X, const void
  * restores the normal limit (the default). */
 dsbcg_status dsbcg_debug_first_wait(dsbcg_ctx* ctx, int polls);
 
+/* Test hook for the chunked shift update; not for production use.  The
+ * per-shift recurrences x_j += p_j u_j, p_j <- v - p_j l_j (Sec. 3) run over
+ * chunks of up to 16 block steps with p_j and x_j held on chip, and give
+ * bitwise the same result for every chunk length.  steps in 1..16 caps the
+ * chunk length of the following inner solves (1: one launch per block step);
+ * 0 restores the automatic length (the default).  Other values:
+ * DSBCG_ERR_ARG. */
+dsbcg_status dsbcg_debug_shift_chunk(dsbcg_ctx* ctx, int steps);
+
 /* Per-kernel CUDA-event timing inside dsbcg_solve (off by default). */
 dsbcg_status dsbcg_set_profiling(dsbcg_ctx* ctx, int on);
 

@@ -89,6 +89,7 @@ struct Lane {
     // blocks; coefficient tiles and active flags chunk slots) and the last
     // step already folded into P and X
     int chunk = 1, k0 = 0;
+    int chunk_used = 1;                           // the running inner solve's chunk (<= chunk)
     int sfp64 = 1;                                // m x m scalar: FP64 (1) or double-float (0)
     double dtol = 0;
     bool running = false;
@@ -118,6 +119,8 @@ struct dsbcg_ctx {
     // CTAs of an FP64 true-residual stencil launch (0: one per work item);
     // set on first use
     int resid_ctas = -1;
+    // cap on the shift-update chunk (test hook; 0: automatic)
+    int force_chunk = 0;
     int debug_first_wait = -1;           // test hook of the block Gram kernel (dsbcg_debug_first_wait)
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -409,7 +412,7 @@ int ensure_refine_lanes(dsbcg_ctx* c, int want) {
     // a lane's buffers; lanes stop while a tenth of the device (at least
     // 4 GiB) would still be free, so that large lattices keep memory for the
     // caller
-    const int chunk = chunk_steps((size_t)m * fb, 4, 64);
+    const int chunk = chunk_steps((size_t)m * fb, 16, 64);
     const size_t lane_bytes = (c->schur ? 3 : 2) * m * fb + (size_t)(chunk + 1) * m * fb + 2 * m * wb + m * db +
                               gram_partial_doubles(M_MAX) * sizeof(double) + small_state_bytes(1) +
                               (4 + 2 * (size_t)chunk) * tb;
@@ -721,6 +724,7 @@ dsbcg_status lane_start(dsbcg_ctx* c, Lane& L, const void* rhs, int rhs_prec, si
     L.prec = prec;
     L.step = 0;
     L.k0 = 0;
+    L.chunk_used = c->force_chunk > 0 ? std::min(L.chunk, c->force_chunk) : L.chunk;
     L.max_steps = max_steps;
     L.freeze = freeze;
     L.poll_every = poll_every;
@@ -737,7 +741,7 @@ dsbcg_status lane_enqueue(dsbcg_ctx* c, Lane& L) {
     const size_t cb = (wp == P64 ? 16 : 8) * (size_t)M_MAX * M_MAX;    // one coefficient tile
     cudaStream_t st = L.st;
     char* ring = (char*)L.vring;
-    const int C = L.chunk, R = C + 1;
+    const int C = L.chunk_used, R = C + 1;
     auto slot = [&](int k) { return ring + (size_t)(k % R) * m_in * fb; };     // V_k
     // P_j and X_j take the steps L.k0 + 1 .. L.step (the chunk's executed ones)
     auto flush = [&]() {
@@ -1541,6 +1545,12 @@ void dsbcg_destroy(dsbcg_ctx* c) {
         cudaEventDestroy(k.b);
     }
     delete c;
+}
+
+dsbcg_status dsbcg_debug_shift_chunk(dsbcg_ctx* c, int steps) {
+    if (!c || steps < 0 || steps > CTL_HIST) return DSBCG_ERR_ARG;
+    c->force_chunk = steps;
+    return DSBCG_OK;
 }
 
 dsbcg_status dsbcg_debug_first_wait(dsbcg_ctx* c, int polls) {

@@ -95,6 +95,8 @@ def lib():
     L.dsbcg_backward.restype = ip
     L.dsbcg_debug_first_wait.argtypes = [vp, ip]
     L.dsbcg_debug_first_wait.restype = ip
+    L.dsbcg_debug_shift_chunk.argtypes = [vp, ip]
+    L.dsbcg_debug_shift_chunk.restype = ip
     L.dsbcg_set_operator.argtypes = [vp, ip]
     L.dsbcg_set_operator.restype = ip
     L.dsbcg_set_profiling.argtypes = [vp, ip]
@@ -182,6 +184,11 @@ class Context:
         Gram kernel's first wait give up after that many tests; -1 restores
         the normal limit."""
         _check(lib().dsbcg_debug_first_wait(self._ctx, int(polls)), "dsbcg_debug_first_wait")
+
+    def debug_shift_chunk(self, steps):
+        """dsbcg_debug_shift_chunk (test hook): caps the shift-update chunk
+        at `steps` block steps (1..16); 0 restores the automatic length."""
+        _check(lib().dsbcg_debug_shift_chunk(self._ctx, int(steps)), "dsbcg_debug_shift_chunk")
 
     def set_profiling(self, on=True):
         _check(lib().dsbcg_set_profiling(self._ctx, int(bool(on))), "dsbcg_set_profiling")

@@ -40,6 +40,8 @@ def test_host_only_calls(L):
     assert L.dsbcg_solve_rational(None, 1, None, 1, None, 0.0, None, 1e-8, None, None, None, None) == -1
     assert L.dsbcg_backward(None, 1, None, 1, None, None, None, None, 0.0, 1e-8, None, None, None, None, None,
                             None) == -1
+    assert L.dsbcg_debug_shift_chunk(None, 1) == -1
+    assert L.dsbcg_debug_first_wait(None, 0) == -1
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
