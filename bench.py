@@ -156,15 +156,26 @@ def ncu_traffic(kclass):
     return None
 
 
+def strip_comments(src):
+    """C/C++ source without // and /* */ comments and with whitespace runs
+    collapsed (string literals in the kernels hold no comment markers)."""
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return " ".join(src.split())
+
+
 def kernel_source_hash():
     """Hash of the device-code sources (every csrc file but the host
-    orchestration in solver.cu)."""
+    orchestration in solver.cu), comments and whitespace removed: a change
+    to the code invalidates the committed ncu figures, one to a comment does
+    not."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1205_0359_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
         if name.endswith((".cu", ".cuh", ".h")) and name != "solver.cu":
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(f.read())
+            with open(os.path.join(csrc, name), encoding="utf-8") as f:
+                h.update(name.encode())
+                h.update(strip_comments(f.read()).encode())
     return h.hexdigest()[:12]
 
 

@@ -1,12 +1,13 @@
 // Tall-skinny block kernels of the block Lanczos process (Sec. 3):
 //   gram          G = X^H Y (nf x nf) for n x nf field blocks, FP64 result
 //   block_update  W = A V_k - V_k alpha_k - V_{k-1} beta_k^H
+//   update_gram   the block update fused with the Gram W^H W of its result
 //   init_basis    V_1 = B S (FP64 right-hand sides -> storage precision)
-//   shift_update  V_{k+1} = W S;  for every active shift j:
+//   v_update      V_{k+1} = W S
+//   shift_chunk   for every active shift j and every block step of a chunk:
 //                 X_j += P_j Ut_j,  P_j <- V_{k+1} - P_j Lh_j
-//                 (the per-shift short recurrences of Sec. 3, all shifts in
-//                 one pass over HBM), P_j and X_j streamed through shared
-//                 memory with bulk asynchronous copies.
+//                 (the per-shift short recurrences of Sec. 3), P_j and X_j
+//                 held on chip across the chunk.
 // Fields are flat complex n-vectors (internal order); each thread owns rows.
 // Accumulation is in the arithmetic precision of the storage (FP32 for
 // FP32/BF16/FP16 fields), reduced across threads in that precision and
@@ -394,17 +395,9 @@ __global__ void __launch_bounds__(256) init_basis_kernel(typename Tr<P>::S2* __r
 }
 
 // ---------------------------------------------------------------------------
-// Shift update (the per-shift short recurrences of Sec. 3 for all shifts,
-// one pass over HBM per operand):
-//     V_{k+1} = W S                       (v_update_kernel, one thread per row)
-//     for every active shift j:
-//     X_j += P_j Ut_j,   P_j <- V_{k+1} - P_j Lh_j   (shift_tile_kernel)
-// shift_tile_kernel runs one CTA per (row tile, shift); its tiles arrive by
-// bulk asynchronous copies (cp.async.bulk, completion on an mbarrier) and
-// each thread updates two rows.  Every mbarrier wait is bounded; on timeout
-// the kernel records an error in the control block, drains its own copies
-// and returns.  For the first step of an inner solve (k == 1) the search
-// block is P_j = V_1 itself.
+// Bulk asynchronous copies and bounded mbarrier waits (the staged Gram).
+// Every mbarrier wait is bounded; on timeout the kernel records an error in
+// the control block, drains its own copies and returns.
 constexpr int ST_WAIT_TIMEOUT = -3;        // reported to the host as DSBCG_ERR_CUDA
 constexpr long MBAR_SPIN_LIMIT = 1L << 22;
 
